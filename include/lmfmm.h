@@ -1,0 +1,172 @@
+/*
+ * lmfmm -- GPU fast multipole method for the interface-induced reaction field
+ * of the electric dyadic Green's function of Maxwell's equations in a
+ * horizontally layered medium (Yuan, Wang, Zhang, Cai, "Fast Multipole method
+ * for Maxwell's equations in layered media", arXiv 2507.18491).
+ *
+ * Plain C ABI: no C++ or framework types cross it.  All complex numbers are
+ * interleaved (re, im) pairs of double.  Every function returns an lmfmm_status
+ * (0 = success, negative = error) unless stated otherwise; on error,
+ * lmfmm_last_error() returns a one-line description for that context.
+ *
+ * Physical conventions (Section 3.1): omega = 1 and mu_l = 1 in every layer,
+ * so eps_l = k_l^2; layers are numbered 0..L from top to bottom; interface
+ * d_l separates layers l and l+1 and d_0 > d_1 > ... > d_{L-1}; every layer
+ * wavenumber has Im k_l >= 0.
+ *
+ * What a matvec computes (eq. layeredmediafields with eq. allcomponents,
+ * reaction part, summed over the first Green's-function slot as the paper
+ * does):
+ *     Phi(r_i) = sum_j sum_{(l,l',*,star)} G^{*star}_{l l'}(r_j, r_i) J_j,
+ * over every point j (self term j = i included) and every reaction component
+ * whose source layer l holds r_j and whose target layer l' holds r_i.
+ *
+ * Ownership: the caller owns every buffer it passes; the library owns the
+ * tree, the translation tables and its work arrays (device memory it
+ * allocates in lmfmm_build and frees in lmfmm_destroy).  Calls on one context
+ * are stream-ordered on the stream passed in (NULL = the legacy default
+ * stream) and a context must not be used from two host threads at once.
+ */
+#ifndef LMFMM_H
+#define LMFMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LMFMM_OK = 0,
+    LMFMM_ERR_ARG = -1,          /* invalid argument (NaN, point on an interface, Im k < 0,
+                                    non-decreasing interfaces, p out of range, NULL) */
+    LMFMM_ERR_CUDA = -2,         /* a CUDA runtime call failed */
+    LMFMM_ERR_OOM = -3,          /* device allocation failed */
+    LMFMM_ERR_STATE = -4,        /* calls made in the wrong order */
+    LMFMM_ERR_QUAD = -5,         /* a bounded device quadrature loop hit its cap */
+    LMFMM_ERR_UNSUPPORTED = -6   /* request outside what this build implements */
+} lmfmm_status;
+
+typedef struct lmfmm_ctx lmfmm_ctx;
+
+typedef struct {
+    double re, im;
+} lmfmm_c128;
+
+enum { LMFMM_FP64 = 0, LMFMM_MIXED = 1 };
+
+typedef struct {
+    int p;             /* truncation order of the expansions, 1..20 (P = (p+1)^2 coefficients) */
+    int depth;         /* octree leaf level (root = 0); < 0 selects it from leaf_cap */
+    int leaf_cap;      /* target points per leaf when depth < 0 */
+    double theta;      /* admissibility: box pair is far if r_s + r_t <= theta * |c_s - c_t|
+                          (centres mapped to images / effective locations) */
+    double eta;        /* ... and its vertical transmission distance is >= eta * |c_s - c_t| */
+    double quad_tol;   /* relative cut-off of the k_rho tails (>= 1e-16) */
+    int precision;     /* LMFMM_FP64 or LMFMM_MIXED (FP32 translation arithmetic) */
+} lmfmm_params;
+
+typedef struct {
+    int64_t n_points;
+    int n_layers;
+    int n_components;      /* active reaction components (l, l', *, star) */
+    int depth;
+    int64_t n_boxes;       /* non-empty boxes, all layers and levels */
+    int64_t n_m2l_pairs;   /* far box pairs, summed over components */
+    int64_t n_geometries;  /* distinct (level, rho, z_s, z_t) M2L tables */
+    int64_t n_near_pairs;  /* near box pairs */
+    int64_t n_near_point_pairs;
+    int64_t n_quad_nodes;  /* k_rho nodes summed over all tabulated geometries */
+    double bytes_tables;   /* device bytes held by M2L tables */
+    double ms_setup;       /* wall time of the last lmfmm_build */
+    double ms_stage[8];    /* last matvec: P2M, M2M, M2L, L2L, L2P, S2T, permute, total */
+    int64_t m2l_columns;   /* helical columns pushed through M2L tables per matvec */
+} lmfmm_stats;
+
+/* Fill *prm with defaults (p = 8, depth from leaf_cap = 64, theta = 0.55,
+ * eta = 0.1, quad_tol = 1e-15, FP64). */
+lmfmm_status lmfmm_default_params(lmfmm_params *prm);
+
+/* Create a context on CUDA device `device`.  *out receives the handle. */
+lmfmm_status lmfmm_create(lmfmm_ctx **out, const lmfmm_params *prm, int device);
+
+/* Layered medium (Section 3.1): L interfaces d[0..L) (host, strictly
+ * decreasing), L+1 layer wavenumbers k[0..L] (host, Im k >= 0, k != 0).
+ * L may be 0 (homogeneous space: no reaction field). */
+lmfmm_status lmfmm_set_layers(lmfmm_ctx *ctx, int L, const double *d, const lmfmm_c128 *k);
+
+/* N points xyz[N][3] (host, row-major doubles).  A point closer than 1e-12
+ * (relative to the domain size) to an interface is ERR_ARG.  Invalidates
+ * any previous build. */
+lmfmm_status lmfmm_set_points(lmfmm_ctx *ctx, int64_t N, const double *xyz);
+
+/* Setup: per-layer octrees, dual-tree traversal of every reaction component
+ * into far (M2L) and near (direct) box pairs, deduplication of M2L
+ * geometries, device tabulation of the M2L Sommerfeld integrals (Section 3.4)
+ * and of the near-field integrals, translation matrices.  Synchronous. */
+lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream);
+
+/* Phi = A J with A the reaction-field operator above.  J[N][3] and Phi[N][3]
+ * are DEVICE pointers to complex doubles in the caller's point order; Phi is
+ * overwritten.  Asynchronous on `stream`. */
+lmfmm_status lmfmm_matvec(lmfmm_ctx *ctx, const lmfmm_c128 *J, lmfmm_c128 *Phi, void *stream);
+
+/* Same operator with HOST buffers J[N][3], Phi[N][3]: copies in, applies,
+ * copies out; returns after Phi is written.  Pinned host memory is faster. */
+lmfmm_status lmfmm_matvec_host(lmfmm_ctx *ctx, const lmfmm_c128 *J, lmfmm_c128 *Phi,
+                               void *stream);
+
+/* Phi = A^H y (device buffers).  The reaction operator is complex symmetric
+ * (reciprocity, G(r,r') = G(r',r)^T, which the paper invokes for summing over
+ * the first slot), so A^H y = conj(A conj(y)); this applies exactly that. */
+lmfmm_status lmfmm_matvec_adjoint(lmfmm_ctx *ctx, const lmfmm_c128 *y, lmfmm_c128 *Phi,
+                                  void *stream);
+
+/* Direct evaluation of the same operator over ALL point pairs with the
+ * device near-field kernel (Sommerfeld integral per pair, Section 3.5);
+ * O(N^2), intended for N up to a few thousand.  Device buffers. */
+lmfmm_status lmfmm_direct(lmfmm_ctx *ctx, const lmfmm_c128 *J, lmfmm_c128 *Phi, void *stream);
+
+/* Density functions phi^{*star}_{l lp}, psi^{*star}_{l lp} (eq. threedensity)
+ * at n nodes krho[n] (DEVICE, complex).  out[n][8] (DEVICE): phi for
+ * (up,up),(up,dn),(dn,up),(dn,dn) then psi in the same order, where the first
+ * arrow is the direction at the target (first slot, layer l) and the second
+ * at the source (second slot, layer lp).  Requires lmfmm_set_layers. */
+lmfmm_status lmfmm_densities(lmfmm_ctx *ctx, int l, int lp, int64_t n, const lmfmm_c128 *krho,
+                             lmfmm_c128 *out, void *stream);
+
+/* Sommerfeld integrals I-hat (eq. onedimensionintegral) of one M2L geometry
+ * for component (l, lp, tgt_up, src_up), via the Chebyshev expansion of
+ * Section 3.4 (eqs. legendre_Q_v/w, chebyshev_integral_I).  out (DEVICE)
+ * [5][P][P] complex, P = (p+1)^2, tables in the order (sigma1,kappa 0),
+ * (sigma5,0), (sigma2,1), (sigma4,1), (sigma3,2); row = target index
+ * nu^2+nu+mu, column = source index n^2+n+m; Bessel order m - mu + kappa.
+ * (rho, zs, zt): horizontal distance and heights of the source and target
+ * centres after mapping to image / effective coordinates. */
+lmfmm_status lmfmm_m2l_table(lmfmm_ctx *ctx, int l, int lp, int tgt_up, int src_up, double rho,
+                             double zs, double zt, lmfmm_c128 *out, void *stream);
+
+/* Host-only (no device, no context): the M2M and L2L matrices of the
+ * regular expansions used by the reaction-field FMM (Section 3.3 notes that
+ * the layered ME/LE bases are those of the Helmholtz equation, so M2M/L2L
+ * are eqs. maxwell_M2M_freespace / maxwell_L2L_freespace).  For wavenumber k
+ * and shift t = child centre - parent centre (t[3], host):
+ *   m2m[P][P]: parent ME = m2m * child ME,   l2l[P][P]: child LE = l2l * parent LE,
+ * row-major, index n^2+n+m, P = (p+1)^2, 1 <= p <= 16; host arrays owned by
+ * the caller.  Built from the addition theorem with exact Gaunt
+ * coefficients, so small entries are accurate relative to their own size. */
+lmfmm_status lmfmm_translation_matrix(int p, lmfmm_c128 k, const double *t, lmfmm_c128 *m2m,
+                                      lmfmm_c128 *l2l);
+
+lmfmm_status lmfmm_get_stats(const lmfmm_ctx *ctx, lmfmm_stats *out);
+
+/* Never NULL; valid until the next call on ctx.  ctx may be NULL (creation
+ * errors). */
+const char *lmfmm_last_error(const lmfmm_ctx *ctx);
+
+void lmfmm_destroy(lmfmm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LMFMM_H */

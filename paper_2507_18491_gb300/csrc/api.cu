@@ -1,0 +1,772 @@
+// The C ABI (include/lmfmm.h): context, validation, device setup (tree
+// upload, M2L tabulation, translation matrices, near-field precomputation)
+// and the matvec pipeline P2M -> M2M -> M2L -> L2L -> L2P (+ S2T).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "kernels.cuh"
+#include "quad.cuh"
+
+using namespace lmf;
+
+namespace {
+
+thread_local std::string g_err;
+
+struct DevState {
+    std::vector<void *> allocs;
+    double *xyz = nullptr;           // sorted [N][3]
+    int64_t *perm = nullptr;
+    BoxDev *boxes = nullptr;
+    int64_t *leaves = nullptr;
+    int64_t nleaves = 0;
+    cd *qh = nullptr, *ph = nullptr; // helical, sorted [N][3]
+    cd *me = nullptr, *le = nullptr; // [nbox][3][P]
+    CompDev *comps = nullptr;
+    GeomDev *geoms = nullptr;
+    cd *tab = nullptr;
+    M2LPair *m2l = nullptr;
+    M2LWork *m2lwork = nullptr;
+    int64_t n_m2lwork = 0;
+    cd *tup = nullptr, *tdn = nullptr;
+    int64_t *tchild = nullptr, *tparent = nullptr;
+    GemmWork *gwork = nullptr;
+    std::vector<int64_t> gwork_off;  // per child level: [off[l], off[l+1])
+    NearPair *near = nullptr;
+    cd *s2t = nullptr;
+    int *flag = nullptr;
+    cd *stage = nullptr;             // [2][N][3] for host-buffer matvec
+    cudaEvent_t ev[9]{};
+    bool ev_ok = false;
+    double bytes = 0;
+};
+
+DevState *DS(lmfmm_ctx *c) { return (DevState *)c->dev; }
+
+#define CK(call)                                                                           \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            ctx->err = std::string(#call) + ": " + cudaGetErrorString(e_);                 \
+            return e_ == cudaErrorMemoryAllocation ? LMFMM_ERR_OOM : LMFMM_ERR_CUDA;       \
+        }                                                                                  \
+    } while (0)
+
+void free_dev(lmfmm_ctx *ctx)
+{
+    DevState *d = DS(ctx);
+    if (!d) return;
+    cudaSetDevice(ctx->device);
+    for (void *p : d->allocs) cudaFree(p);
+    d->allocs.clear();
+    if (d->ev_ok)
+        for (auto &e : d->ev) cudaEventDestroy(e);
+    delete d;
+    ctx->dev = nullptr;
+}
+
+template <typename T>
+lmfmm_status dalloc(lmfmm_ctx *ctx, T **p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+    if (e != cudaSuccess) {
+        ctx->err = "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes: " +
+                   cudaGetErrorString(e);
+        return LMFMM_ERR_OOM;
+    }
+    DS(ctx)->allocs.push_back(q);
+    DS(ctx)->bytes += (double)(count * sizeof(T));
+    *p = (T *)q;
+    return LMFMM_OK;
+}
+
+template <typename T>
+lmfmm_status dupload(lmfmm_ctx *ctx, T **p, const std::vector<T> &h)
+{
+    lmfmm_status s = dalloc(ctx, p, h.size());
+    if (s) return s;
+    if (!h.empty()) CK(cudaMemcpy(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return LMFMM_OK;
+}
+
+#define TRY(x)                        \
+    do {                              \
+        lmfmm_status s_ = (x);        \
+        if (s_ != LMFMM_OK) return s_; \
+    } while (0)
+
+double medium_a(const MediumDev &M)
+{
+    double km = 0;
+    for (int j = 0; j <= M.L; ++j) km = std::max(km, std::hypot(M.k[j].x, M.k[j].y));
+    return 1.5 * km + 0.75;
+}
+
+// k_rho quadrature plan of an M2L geometry: the Chebyshev integrands carry
+// a polynomial of degree up to 2p+5 in k_rho.
+QuadPlanDev geom_plan(double a, int p, double rho, double dz) { return make_plan(a, rho, dz, 2 * p + 5); }
+
+lmfmm_status check_flag(lmfmm_ctx *ctx)
+{
+    int f = 0;
+    CK(cudaMemcpy(&f, DS(ctx)->flag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (f) {
+        ctx->err = "device quadrature hit its cap (flag " + std::to_string(f) + ")";
+        return LMFMM_ERR_QUAD;
+    }
+    return LMFMM_OK;
+}
+
+// Tabulate a list of geometries into `tab` (device), batching node factors
+// and Chebyshev integrals through a scratch buffer.
+lmfmm_status tabulate(lmfmm_ctx *ctx, std::vector<GeomDev> &hg, const CompDev *dcomps,
+                      const cd *dG, const int *dcg, cd *tab, cudaStream_t st)
+{
+    const int p = ctx->prm.p;
+    const int LM = p + 2, DJ = 2 * p + 3;
+    const int64_t per_node = 5 + 4 + 4 + LM + DJ;
+    const int64_t ibr = (int64_t)NTAB * 4 * 4 * LM * DJ;
+    const size_t scratch_bytes = (size_t)1 << 30;
+    // batches
+    std::vector<int> bstart;
+    std::vector<int64_t> bstride;
+    int ng = (int)hg.size();
+    int g = 0;
+    while (g < ng) {
+        int64_t nodes = 0;
+        int gb = g;
+        while (gb < ng) {
+            int64_t q = plan_nodes(hg[gb].plan);
+            int64_t need = (nodes + q) * per_node + (int64_t)(gb - g + 1) * ibr;
+            if ((size_t)need * sizeof(cd) > scratch_bytes && gb > g) break;
+            hg[gb].node0 = nodes;
+            nodes += q;
+            ++gb;
+            if (gb - g >= 2048) break;
+        }
+        for (int i = g; i < gb; ++i) hg[i].stride = nodes;
+        bstart.push_back(g);
+        bstride.push_back(nodes);
+        g = gb;
+    }
+    bstart.push_back(ng);
+    size_t need_max = 0;
+    for (size_t b = 0; b + 1 < bstart.size(); ++b)
+        need_max = std::max(need_max, (size_t)(bstride[b] * per_node +
+                                               (int64_t)(bstart[b + 1] - bstart[b]) * ibr));
+    GeomDev *dgeo = nullptr;
+    cd *scr = nullptr;
+    void *qg = nullptr, *qs = nullptr;
+    CK(cudaMalloc(&qg, std::max<size_t>(1, hg.size()) * sizeof(GeomDev)));
+    dgeo = (GeomDev *)qg;
+    cudaError_t e = cudaMalloc(&qs, std::max<size_t>(1, need_max) * sizeof(cd));
+    if (e != cudaSuccess) {
+        cudaFree(qg);
+        ctx->err = "tabulation scratch allocation failed";
+        return LMFMM_ERR_OOM;
+    }
+    scr = (cd *)qs;
+    lmfmm_status rc = LMFMM_OK;
+    if (!hg.empty() &&
+        cudaMemcpy(dgeo, hg.data(), hg.size() * sizeof(GeomDev), cudaMemcpyHostToDevice))
+        rc = LMFMM_ERR_CUDA;
+    for (size_t b = 0; rc == LMFMM_OK && b + 1 < bstart.size(); ++b) {
+        int g0 = bstart[b], nb = bstart[b + 1] - g0;
+        int qmax = 0;
+        for (int i = g0; i < g0 + nb; ++i) qmax = std::max(qmax, plan_nodes(hg[i].plan));
+        launch_tab_batch(dgeo, g0, nb, qmax, ctx->med, dcomps, p, dG, dcg, scr, bstride[b], tab,
+                         DS(ctx)->flag, st);
+        if (cudaGetLastError() != cudaSuccess) rc = LMFMM_ERR_CUDA;
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess) rc = LMFMM_ERR_CUDA;
+    cudaFree(qg);
+    cudaFree(qs);
+    if (rc) {
+        ctx->err = "tabulation kernels failed";
+        return rc;
+    }
+    return check_flag(ctx);
+}
+
+}  // namespace
+
+// --------------------------------------------------------------------- ABI
+extern "C" {
+
+lmfmm_status lmfmm_default_params(lmfmm_params *prm)
+{
+    if (!prm) return LMFMM_ERR_ARG;
+    prm->p = 8;
+    prm->depth = -1;
+    prm->leaf_cap = 64;
+    prm->theta = 0.55;
+    prm->eta = 0.1;
+    prm->quad_tol = 1e-15;
+    prm->precision = LMFMM_FP64;
+    return LMFMM_OK;
+}
+
+lmfmm_status lmfmm_create(lmfmm_ctx **out, const lmfmm_params *prm, int device)
+{
+    if (!out || !prm) {
+        g_err = "lmfmm_create: NULL argument";
+        return LMFMM_ERR_ARG;
+    }
+    *out = nullptr;
+    if (prm->p < 1 || prm->p > 16 || !(prm->theta > 0 && prm->theta < 1) || !(prm->eta >= 0) ||
+        prm->depth > 20 || (prm->depth < 0 && prm->leaf_cap < 1)) {
+        g_err = "lmfmm_create: parameter out of range (1 <= p <= 16, 0 < theta < 1, eta >= 0, "
+                "depth <= 20)";
+        return LMFMM_ERR_ARG;
+    }
+    if (prm->precision != LMFMM_FP64) {
+        g_err = "lmfmm_create: only LMFMM_FP64 is implemented in this build";
+        return LMFMM_ERR_UNSUPPORTED;
+    }
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) {
+        g_err = std::string("cudaSetDevice: ") + cudaGetErrorString(e);
+        return LMFMM_ERR_CUDA;
+    }
+    if ((e = configure_fmm_kernels()) != cudaSuccess || (e = configure_tab_kernels()) != cudaSuccess) {
+        g_err = std::string("kernel configuration: ") + cudaGetErrorString(e);
+        return LMFMM_ERR_CUDA;
+    }
+    lmfmm_ctx *ctx = new lmfmm_ctx();
+    ctx->device = device;
+    ctx->prm = *prm;
+    *out = ctx;
+    return LMFMM_OK;
+}
+
+lmfmm_status lmfmm_set_layers(lmfmm_ctx *ctx, int L, const double *d, const lmfmm_c128 *k)
+{
+    if (!ctx) return LMFMM_ERR_ARG;
+    if (L < 0 || L > LMF_MAXL || (L > 0 && !d) || !k) {
+        ctx->err = "set_layers: need 0 <= L <= " + std::to_string(LMF_MAXL) + " and non-NULL arrays";
+        return LMFMM_ERR_ARG;
+    }
+    for (int i = 0; i < L; ++i) {
+        if (!std::isfinite(d[i]) || (i > 0 && !(d[i] < d[i - 1]))) {
+            ctx->err = "set_layers: interfaces must be finite and strictly decreasing";
+            return LMFMM_ERR_ARG;
+        }
+    }
+    for (int i = 0; i <= L; ++i) {
+        if (!std::isfinite(k[i].re) || !std::isfinite(k[i].im) || k[i].im < 0 ||
+            (k[i].re == 0 && k[i].im == 0)) {
+            ctx->err = "set_layers: wavenumber " + std::to_string(i) + " must be finite, nonzero, Im >= 0";
+            return LMFMM_ERR_ARG;
+        }
+    }
+    ctx->med = MediumDev{};
+    ctx->med.L = L;
+    for (int i = 0; i < L; ++i) ctx->med.d[i] = d[i];
+    for (int i = 0; i <= L; ++i) ctx->med.k[i] = cd{k[i].re, k[i].im};
+    ctx->layers_set = true;
+    ctx->built = false;
+    return LMFMM_OK;
+}
+
+lmfmm_status lmfmm_set_points(lmfmm_ctx *ctx, int64_t N, const double *xyz)
+{
+    if (!ctx) return LMFMM_ERR_ARG;
+    if (!ctx->layers_set) {
+        ctx->err = "set_points: call lmfmm_set_layers first";
+        return LMFMM_ERR_STATE;
+    }
+    if (N < 1 || !xyz) {
+        ctx->err = "set_points: need N >= 1 and a non-NULL array";
+        return LMFMM_ERR_ARG;
+    }
+    ctx->N = N;
+    ctx->xyz.assign(xyz, xyz + 3 * N);
+    ctx->built = false;
+    lmfmm_status s = classify_and_sort(ctx);
+    ctx->points_set = (s == LMFMM_OK);
+    return s;
+}
+
+lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
+{
+    if (!ctx) return LMFMM_ERR_ARG;
+    if (!ctx->points_set) {
+        ctx->err = "build: call lmfmm_set_points first";
+        return LMFMM_ERR_STATE;
+    }
+    auto t0 = std::chrono::steady_clock::now();
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    free_dev(ctx);
+    ctx->dev = new DevState();
+    DevState *d = DS(ctx);
+    ctx->built = false;
+    TRY(build_host_structures(ctx));
+    chebyshev_tables(ctx);
+    const int p = ctx->prm.p, P = (p + 1) * (p + 1);
+    const int64_t N = ctx->N, nbox = (int64_t)ctx->boxes.size();
+    // memory estimate (tables dominate)
+    double need = (double)ctx->geoms.size() * NTAB * P * P * 16.0 +
+                  (double)nbox * 6 * P * 16.0 + (double)ctx->tgroups.size() * 2 * P * P * 16.0 +
+                  (double)ctx->n_near_pp * 5 * 16.0 + (double)N * 200.0;
+    size_t fr = 0, tot = 0;
+    CK(cudaMemGetInfo(&fr, &tot));
+    if (need > 0.85 * (double)fr) {
+        ctx->err = "build: needs about " + std::to_string(need / 1e9) + " GB of device memory, " +
+                   std::to_string(fr / 1e9) + " GB free (reduce p or raise theta/depth)";
+        return LMFMM_ERR_OOM;
+    }
+    CK(cudaMalloc((void **)&d->flag, sizeof(int)));
+    d->allocs.push_back(d->flag);
+    CK(cudaMemset(d->flag, 0, sizeof(int)));
+    for (auto &e : d->ev) CK(cudaEventCreate(&e));
+    d->ev_ok = true;
+    // points and boxes
+    TRY(dupload(ctx, &d->xyz, ctx->sxyz));
+    TRY(dupload(ctx, &d->perm, ctx->perm));
+    std::vector<BoxDev> hb(nbox);
+    std::vector<int64_t> leaves;
+    for (int64_t i = 0; i < nbox; ++i) {
+        const Box &b = ctx->boxes[i];
+        hb[i] = BoxDev{b.p0, b.p1, {b.c[0], b.c[1], b.c[2]}, b.layer, 0};
+        if (b.level == ctx->depth) leaves.push_back(i);
+    }
+    TRY(dupload(ctx, &d->boxes, hb));
+    TRY(dupload(ctx, &d->leaves, leaves));
+    d->nleaves = (int64_t)leaves.size();
+    TRY(dalloc(ctx, &d->qh, 3 * N));
+    TRY(dalloc(ctx, &d->ph, 3 * N));
+    TRY(dalloc(ctx, &d->me, (size_t)nbox * 3 * P));
+    TRY(dalloc(ctx, &d->le, (size_t)nbox * 3 * P));
+    TRY(dupload(ctx, &d->comps, ctx->comps));
+    cd *dG = nullptr;
+    int *dcg = nullptr;
+    TRY(dupload(ctx, &dG, ctx->Gten));
+    TRY(dupload(ctx, &dcg, ctx->comp_gidx));
+    // M2L geometries, tables and work items
+    const double a = medium_a(ctx->med);
+    std::vector<GeomDev> hg(ctx->geoms.size());
+    int64_t qtot = 0;
+    for (size_t i = 0; i < ctx->geoms.size(); ++i) {
+        const Geom &g = ctx->geoms[i];
+        const CompDev &c = ctx->comps[g.comp];
+        GeomDev gd{};
+        gd.comp = g.comp;
+        gd.src_primary = std::hypot(ctx->med.k[c.l].x, ctx->med.k[c.l].y) <=
+                         std::hypot(ctx->med.k[c.lp].x, ctx->med.k[c.lp].y);
+        gd.rho = g.rho;
+        gd.zs = g.zs;
+        gd.zt = g.zt;
+        gd.plan = geom_plan(a, p, g.rho, c.s * (g.zs - g.zt));
+        if (plan_nodes(gd.plan) > (1 << 20)) {
+            ctx->err = "build: an M2L geometry needs more than 2^20 quadrature nodes";
+            return LMFMM_ERR_QUAD;
+        }
+        qtot += plan_nodes(gd.plan);
+        gd.tab_index = (int64_t)i;
+        hg[i] = gd;
+    }
+    TRY(dalloc(ctx, &d->tab, ctx->geoms.size() * (size_t)NTAB * P * P));
+    TRY(tabulate(ctx, hg, d->comps, dG, dcg, d->tab, st));
+    TRY(dupload(ctx, &d->geoms, hg));
+    TRY(dupload(ctx, &d->m2l, ctx->m2l));
+    std::vector<M2LWork> mw;
+    int64_t ncols = 0;
+    for (size_t gi = 0; gi < ctx->geoms.size(); ++gi) {
+        const Geom &g = ctx->geoms[gi];
+        for (int t = 0; t < NTAB; ++t) {
+            int per = (t == 1) ? 32 : 16;
+            for (int64_t q = g.pair0; q < g.pair1; q += per) {
+                M2LWork w{};
+                w.geom = (int)gi;
+                w.t = t;
+                w.pair0 = q;
+                w.npair = (int)std::min<int64_t>(per, g.pair1 - q);
+                ncols += w.npair * (t == 1 ? 1 : 2);
+                mw.push_back(w);
+            }
+        }
+    }
+    TRY(dupload(ctx, &d->m2lwork, mw));
+    d->n_m2lwork = (int64_t)mw.size();
+    // translation matrices (exact addition theorem, host)
+    {
+        std::vector<int64_t> goff;
+        std::vector<int> gl;
+        std::vector<double> gv;
+        gaunt_table(p, goff, gl, gv);
+        size_t ngr = ctx->tgroups.size();
+        std::vector<cd> hup(ngr * (size_t)P * P), hdn(ngr * (size_t)P * P);
+        for (size_t i = 0; i < ngr; ++i) {
+            const TransGroup &g = ctx->tgroups[i];
+            translation_matrix(p, zc(ctx->med.k[g.layer].x, ctx->med.k[g.layer].y), g.t, goff, gl,
+                               gv, &hup[i * P * P], &hdn[i * P * P]);
+        }
+        TRY(dupload(ctx, &d->tup, hup));
+        TRY(dupload(ctx, &d->tdn, hdn));
+        TRY(dupload(ctx, &d->tchild, ctx->tpair_child));
+        TRY(dupload(ctx, &d->tparent, ctx->tpair_parent));
+        // work items per child level
+        std::vector<GemmWork> gw;
+        d->gwork_off.assign(ctx->depth + 2, 0);
+        for (int lev = 1; lev <= ctx->depth; ++lev) {
+            d->gwork_off[lev] = (int64_t)gw.size();
+            for (size_t gi = 0; gi < ctx->tgroups.size(); ++gi) {
+                const TransGroup &g = ctx->tgroups[gi];
+                if (g.level != lev) continue;
+                for (int64_t q = g.pair0; q < g.pair1; q += 10)
+                    gw.push_back(GemmWork{(int)gi, (int)std::min<int64_t>(10, g.pair1 - q), q});
+            }
+        }
+        d->gwork_off[ctx->depth + 1] = (int64_t)gw.size();
+        TRY(dupload(ctx, &d->gwork, gw));
+    }
+    // near field
+    TRY(dupload(ctx, &d->near, ctx->near));
+    TRY(dalloc(ctx, &d->s2t, (size_t)ctx->n_near_pp * 5));
+    launch_s2t_pre((int64_t)ctx->near.size(), d->near, d->boxes, d->xyz, ctx->med, d->comps, a,
+                   0.5 * a, d->s2t, d->flag, st);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+    TRY(check_flag(ctx));
+    ctx->built = true;
+    auto t1 = std::chrono::steady_clock::now();
+    lmfmm_stats &S = ctx->stats;
+    S = lmfmm_stats{};
+    S.n_points = N;
+    S.n_layers = ctx->med.L + 1;
+    S.n_components = (int)ctx->comps.size();
+    S.depth = ctx->depth;
+    S.n_boxes = nbox;
+    S.n_m2l_pairs = (int64_t)ctx->m2l.size();
+    S.n_geometries = (int64_t)ctx->geoms.size();
+    S.n_near_pairs = (int64_t)ctx->near.size();
+    S.n_near_point_pairs = ctx->n_near_pp;
+    S.n_quad_nodes = qtot;
+    S.bytes_tables = (double)ctx->geoms.size() * NTAB * P * P * 16.0;
+    S.ms_setup = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    S.m2l_columns = ncols;
+    return LMFMM_OK;
+}
+
+static lmfmm_status matvec_impl(lmfmm_ctx *ctx, const lmfmm_c128 *J, lmfmm_c128 *Phi,
+                                cudaStream_t st, bool cj)
+{
+    DevState *d = DS(ctx);
+    const int p = ctx->prm.p, P = (p + 1) * (p + 1);
+    const int64_t N = ctx->N, nbox = (int64_t)ctx->boxes.size();
+    CK(cudaEventRecord(d->ev[0], st));
+    launch_gather_in(N, d->perm, (const cd *)J, d->qh, cj, st);
+    CK(cudaMemsetAsync(d->me, 0, (size_t)nbox * 3 * P * sizeof(cd), st));
+    launch_p2m(p, d->nleaves, d->leaves, d->boxes, d->xyz, d->qh, ctx->med, d->me, st);
+    CK(cudaEventRecord(d->ev[1], st));
+    for (int lev = ctx->depth; lev >= 1; --lev) {
+        int64_t w0 = d->gwork_off[lev], w1 = d->gwork_off[lev + 1];
+        launch_group_gemm(p, w1 - w0, d->gwork + w0, d->tup, d->tchild, d->tparent, d->me,
+                          d->me, true, st);
+    }
+    CK(cudaEventRecord(d->ev[2], st));
+    CK(cudaMemsetAsync(d->le, 0, (size_t)nbox * 3 * P * sizeof(cd), st));
+    launch_m2l(p, d->n_m2lwork, d->m2lwork, d->geoms, d->comps, d->m2l, d->tab, d->me, d->le, st);
+    CK(cudaEventRecord(d->ev[3], st));
+    for (int lev = 1; lev <= ctx->depth; ++lev) {
+        int64_t w0 = d->gwork_off[lev], w1 = d->gwork_off[lev + 1];
+        launch_group_gemm(p, w1 - w0, d->gwork + w0, d->tdn, d->tparent, d->tchild, d->le,
+                          d->le, false, st);
+    }
+    CK(cudaEventRecord(d->ev[4], st));
+    launch_l2p(p, d->nleaves, d->leaves, d->boxes, d->xyz, d->le, ctx->med, d->ph, st);
+    CK(cudaEventRecord(d->ev[5], st));
+    launch_s2t_apply((int64_t)ctx->near.size(), d->near, d->boxes, d->xyz, d->s2t, d->qh, d->ph,
+                     st);
+    CK(cudaEventRecord(d->ev[6], st));
+    launch_scatter_out(N, d->perm, d->ph, (cd *)Phi, cj, st);
+    CK(cudaEventRecord(d->ev[7], st));
+    CK(cudaGetLastError());
+    return LMFMM_OK;
+}
+
+lmfmm_status lmfmm_matvec(lmfmm_ctx *ctx, const lmfmm_c128 *J, lmfmm_c128 *Phi, void *stream)
+{
+    if (!ctx) return LMFMM_ERR_ARG;
+    if (!ctx->built) {
+        ctx->err = "matvec: call lmfmm_build first";
+        return LMFMM_ERR_STATE;
+    }
+    if (!J || !Phi) {
+        ctx->err = "matvec: NULL buffer";
+        return LMFMM_ERR_ARG;
+    }
+    CK(cudaSetDevice(ctx->device));
+    return matvec_impl(ctx, J, Phi, (cudaStream_t)stream, false);
+}
+
+lmfmm_status lmfmm_matvec_adjoint(lmfmm_ctx *ctx, const lmfmm_c128 *y, lmfmm_c128 *Phi,
+                                  void *stream)
+{
+    if (!ctx) return LMFMM_ERR_ARG;
+    if (!ctx->built) {
+        ctx->err = "matvec_adjoint: call lmfmm_build first";
+        return LMFMM_ERR_STATE;
+    }
+    if (!y || !Phi) {
+        ctx->err = "matvec_adjoint: NULL buffer";
+        return LMFMM_ERR_ARG;
+    }
+    CK(cudaSetDevice(ctx->device));
+    return matvec_impl(ctx, y, Phi, (cudaStream_t)stream, true);
+}
+
+lmfmm_status lmfmm_matvec_host(lmfmm_ctx *ctx, const lmfmm_c128 *J, lmfmm_c128 *Phi, void *stream)
+{
+    if (!ctx) return LMFMM_ERR_ARG;
+    if (!ctx->built) {
+        ctx->err = "matvec_host: call lmfmm_build first";
+        return LMFMM_ERR_STATE;
+    }
+    if (!J || !Phi) {
+        ctx->err = "matvec_host: NULL buffer";
+        return LMFMM_ERR_ARG;
+    }
+    CK(cudaSetDevice(ctx->device));
+    DevState *d = DS(ctx);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = (size_t)ctx->N * 3 * sizeof(cd);
+    if (!d->stage) TRY(dalloc(ctx, &d->stage, (size_t)ctx->N * 6));
+    CK(cudaMemcpyAsync(d->stage, J, bytes, cudaMemcpyHostToDevice, st));
+    TRY(matvec_impl(ctx, (const lmfmm_c128 *)d->stage, (lmfmm_c128 *)(d->stage + 3 * ctx->N), st,
+                    false));
+    CK(cudaMemcpyAsync(Phi, d->stage + 3 * ctx->N, bytes, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return LMFMM_OK;
+}
+
+lmfmm_status lmfmm_direct(lmfmm_ctx *ctx, const lmfmm_c128 *J, lmfmm_c128 *Phi, void *stream)
+{
+    if (!ctx) return LMFMM_ERR_ARG;
+    if (!ctx->built) {
+        ctx->err = "direct: call lmfmm_build first";
+        return LMFMM_ERR_STATE;
+    }
+    if (!J || !Phi) {
+        ctx->err = "direct: NULL buffer";
+        return LMFMM_ERR_ARG;
+    }
+    CK(cudaSetDevice(ctx->device));
+    DevState *d = DS(ctx);
+    cudaStream_t st = (cudaStream_t)stream;
+    // every (component, source leaf, target leaf) pair is treated as near
+    std::vector<NearPair> all;
+    int64_t npp = 0;
+    for (int ci = 0; ci < (int)ctx->comps.size(); ++ci) {
+        const CompDev &c = ctx->comps[ci];
+        int D = ctx->depth;
+        for (int64_t bs = ctx->lvl0[c.l][D]; bs < ctx->lvl1[c.l][D]; ++bs)
+            for (int64_t bt = ctx->lvl0[c.lp][D]; bt < ctx->lvl1[c.lp][D]; ++bt) {
+                const Box &B = ctx->boxes[bs], &C = ctx->boxes[bt];
+                double smn = 1e300, smx = -1e300, tmn = 1e300, tmx = -1e300;
+                double bl[2] = {1e300, 1e300}, bh[2] = {-1e300, -1e300}, cl[2] = {1e300, 1e300},
+                       ch[2] = {-1e300, -1e300};
+                for (int64_t t = B.p0; t < B.p1; ++t) {
+                    double z = comp_src_z(c, ctx->sxyz[3 * t + 2]);
+                    smn = std::min(smn, z);
+                    smx = std::max(smx, z);
+                    for (int e = 0; e < 2; ++e) {
+                        bl[e] = std::min(bl[e], ctx->sxyz[3 * t + e]);
+                        bh[e] = std::max(bh[e], ctx->sxyz[3 * t + e]);
+                    }
+                }
+                for (int64_t t = C.p0; t < C.p1; ++t) {
+                    double z = comp_tgt_z(c, ctx->sxyz[3 * t + 2]);
+                    tmn = std::min(tmn, z);
+                    tmx = std::max(tmx, z);
+                    for (int e = 0; e < 2; ++e) {
+                        cl[e] = std::min(cl[e], ctx->sxyz[3 * t + e]);
+                        ch[e] = std::max(ch[e], ctx->sxyz[3 * t + e]);
+                    }
+                }
+                NearPair np{};
+                np.comp = ci;
+                np.src = bs;
+                np.tgt = bt;
+                np.coef0 = npp;
+                np.dzmin = c.s > 0 ? smn - tmx : tmn - smx;
+                double mx = std::max(std::fabs(bh[0] - cl[0]), std::fabs(ch[0] - bl[0]));
+                double my = std::max(std::fabs(bh[1] - cl[1]), std::fabs(ch[1] - bl[1]));
+                np.rhomax = std::sqrt(mx * mx + my * my);
+                npp += (B.p1 - B.p0) * (C.p1 - C.p0);
+                all.push_back(np);
+            }
+    }
+    NearPair *dn = nullptr;
+    cd *coef = nullptr;
+    void *q1 = nullptr, *q2 = nullptr;
+    CK(cudaMalloc(&q1, std::max<size_t>(1, all.size()) * sizeof(NearPair)));
+    dn = (NearPair *)q1;
+    if (cudaMalloc(&q2, std::max<int64_t>(1, npp) * 5 * sizeof(cd)) != cudaSuccess) {
+        cudaFree(q1);
+        ctx->err = "direct: coefficient allocation failed";
+        return LMFMM_ERR_OOM;
+    }
+    coef = (cd *)q2;
+    lmfmm_status rc = LMFMM_OK;
+    if (!all.empty() &&
+        cudaMemcpy(dn, all.data(), all.size() * sizeof(NearPair), cudaMemcpyHostToDevice))
+        rc = LMFMM_ERR_CUDA;
+    if (!rc) {
+        double a = medium_a(ctx->med);
+        launch_gather_in(ctx->N, d->perm, (const cd *)J, d->qh, false, st);
+        cudaMemsetAsync(d->ph, 0, (size_t)ctx->N * 3 * sizeof(cd), st);
+        launch_s2t_pre((int64_t)all.size(), dn, d->boxes, d->xyz, ctx->med, d->comps, a, 0.5 * a,
+                       coef, d->flag, st);
+        launch_s2t_apply((int64_t)all.size(), dn, d->boxes, d->xyz, coef, d->qh, d->ph, st);
+        launch_scatter_out(ctx->N, d->perm, d->ph, (cd *)Phi, false, st);
+        if (cudaStreamSynchronize(st) != cudaSuccess) rc = LMFMM_ERR_CUDA;
+    }
+    cudaFree(q1);
+    cudaFree(q2);
+    if (rc) {
+        ctx->err = "direct: CUDA failure";
+        return rc;
+    }
+    return check_flag(ctx);
+}
+
+lmfmm_status lmfmm_densities(lmfmm_ctx *ctx, int l, int lp, int64_t n, const lmfmm_c128 *krho,
+                             lmfmm_c128 *out, void *stream)
+{
+    if (!ctx) return LMFMM_ERR_ARG;
+    if (!ctx->layers_set) {
+        ctx->err = "densities: call lmfmm_set_layers first";
+        return LMFMM_ERR_STATE;
+    }
+    if (l < 0 || lp < 0 || l > ctx->med.L || lp > ctx->med.L || n < 0 || (n > 0 && (!krho || !out))) {
+        ctx->err = "densities: layer index out of range or NULL buffer";
+        return LMFMM_ERR_ARG;
+    }
+    if (ctx->med.L == 0) {
+        ctx->err = "densities: no interfaces";
+        return LMFMM_ERR_ARG;
+    }
+    CK(cudaSetDevice(ctx->device));
+    launch_densities(ctx->med, l, lp, n, (const cd *)krho, (cd *)out, (cudaStream_t)stream);
+    CK(cudaGetLastError());
+    return LMFMM_OK;
+}
+
+lmfmm_status lmfmm_m2l_table(lmfmm_ctx *ctx, int l, int lp, int tgt_up, int src_up, double rho,
+                             double zs, double zt, lmfmm_c128 *out, void *stream)
+{
+    if (!ctx) return LMFMM_ERR_ARG;
+    if (!ctx->layers_set) {
+        ctx->err = "m2l_table: call lmfmm_set_layers first";
+        return LMFMM_ERR_STATE;
+    }
+    const int L = ctx->med.L;
+    if (L < 1 || l < 0 || lp < 0 || l > L || lp > L || !out || !(rho >= 0) ||
+        (tgt_up && l > L - 1) || (!tgt_up && l < 1) || (src_up && lp < 1) || (!src_up && lp > L - 1)) {
+        ctx->err = "m2l_table: no such reaction component or bad argument";
+        return LMFMM_ERR_ARG;
+    }
+    CompDev c{};
+    c.l = l;
+    c.lp = lp;
+    c.tu = tgt_up ? 1 : 0;
+    c.su = src_up ? 1 : 0;
+    c.s = comp_sign(l, lp, c.su);
+    if (!(c.s * (zs - zt) > 0)) {
+        ctx->err = "m2l_table: centres are not separated in the direction of the component";
+        return LMFMM_ERR_ARG;
+    }
+    CK(cudaSetDevice(ctx->device));
+    const int p = ctx->prm.p, T = (p + 1) * (p + 2) / 2;
+    std::vector<double> B;
+    int KM = (p + 1) / 2;
+    bcoef_table(p, KM, B);
+    std::vector<cd> G((size_t)T * T * (p + 2));
+    gtensor(p, B, KM, zc(ctx->med.k[l].x, ctx->med.k[l].y), zc(ctx->med.k[lp].x, ctx->med.k[lp].y),
+            G.data());
+    if (!ctx->dev) ctx->dev = new DevState();
+    DevState *d = DS(ctx);
+    if (!d->flag) {
+        CK(cudaMalloc((void **)&d->flag, sizeof(int)));
+        d->allocs.push_back(d->flag);
+        CK(cudaMemset(d->flag, 0, sizeof(int)));
+    }
+    std::vector<GeomDev> hg(1);
+    hg[0].comp = 0;
+    hg[0].src_primary = std::hypot(ctx->med.k[l].x, ctx->med.k[l].y) <=
+                        std::hypot(ctx->med.k[lp].x, ctx->med.k[lp].y);
+    hg[0].rho = rho;
+    hg[0].zs = zs;
+    hg[0].zt = zt;
+    hg[0].plan = geom_plan(medium_a(ctx->med), p, rho, c.s * (zs - zt));
+    hg[0].tab_index = 0;
+    void *qc = nullptr, *qG = nullptr, *qi = nullptr;
+    CK(cudaMalloc(&qc, sizeof(CompDev)));
+    CK(cudaMalloc(&qG, G.size() * sizeof(cd)));
+    CK(cudaMalloc(&qi, sizeof(int)));
+    int zero = 0;
+    CK(cudaMemcpy(qc, &c, sizeof(CompDev), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(qG, G.data(), G.size() * sizeof(cd), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(qi, &zero, sizeof(int), cudaMemcpyHostToDevice));
+    lmfmm_status rc = tabulate(ctx, hg, (const CompDev *)qc, (const cd *)qG, (const int *)qi,
+                               (cd *)out, (cudaStream_t)stream);
+    cudaFree(qc);
+    cudaFree(qG);
+    cudaFree(qi);
+    return rc;
+}
+
+lmfmm_status lmfmm_translation_matrix(int p, lmfmm_c128 k, const double *t, lmfmm_c128 *m2m,
+                                      lmfmm_c128 *l2l)
+{
+    if (p < 1 || p > 16 || !t || !m2m || !l2l || !std::isfinite(t[0]) || !std::isfinite(t[1]) ||
+        !std::isfinite(t[2])) {
+        g_err = "translation_matrix: bad argument";
+        return LMFMM_ERR_ARG;
+    }
+    std::vector<int64_t> goff;
+    std::vector<int> gl;
+    std::vector<double> gv;
+    gaunt_table(p, goff, gl, gv);
+    translation_matrix(p, zc(k.re, k.im), t, goff, gl, gv, (cd *)m2m, (cd *)l2l);
+    return LMFMM_OK;
+}
+
+lmfmm_status lmfmm_get_stats(const lmfmm_ctx *ctx, lmfmm_stats *out)
+{
+    if (!ctx || !out) return LMFMM_ERR_ARG;
+    lmfmm_ctx *c = (lmfmm_ctx *)ctx;
+    *out = c->stats;
+    DevState *d = DS(c);
+    if (c->built && d && d->ev_ok && cudaEventQuery(d->ev[7]) == cudaSuccess) {
+        float ms;
+        for (int i = 0; i < 6; ++i)
+            if (cudaEventElapsedTime(&ms, d->ev[i], d->ev[i + 1]) == cudaSuccess) out->ms_stage[i] = ms;
+        if (cudaEventElapsedTime(&ms, d->ev[6], d->ev[7]) == cudaSuccess) out->ms_stage[6] = ms;
+        if (cudaEventElapsedTime(&ms, d->ev[0], d->ev[7]) == cudaSuccess) out->ms_stage[7] = ms;
+    }
+    return LMFMM_OK;
+}
+
+const char *lmfmm_last_error(const lmfmm_ctx *ctx)
+{
+    if (!ctx) return g_err.c_str();
+    return ctx->err.c_str();
+}
+
+void lmfmm_destroy(lmfmm_ctx *ctx)
+{
+    if (!ctx) return;
+    free_dev(ctx);
+    delete ctx;
+}
+
+}  // extern "C"

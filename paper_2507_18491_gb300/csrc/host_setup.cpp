@@ -1,0 +1,653 @@
+// Host-side setup: point classification and Morton sort, per-layer octrees
+// on one global grid, enumeration of reaction components, dual-tree traversal
+// of every component into far (M2L) and near box pairs, deduplication of M2L
+// geometries, translation groups, and the Chebyshev coefficient tables of
+// Section 3.4 / Appendices A-B.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <numeric>
+#include <tuple>
+#include <unordered_map>
+
+#include "internal.h"
+
+namespace lmf {
+
+static uint64_t spread3(uint64_t v)
+{
+    uint64_t r = 0;
+    for (int b = 0; b < 21; ++b) r |= ((v >> b) & 1ull) << (3 * b);
+    return r;
+}
+static uint32_t compact3(uint64_t v)
+{
+    uint32_t r = 0;
+    for (int b = 0; b < 21; ++b) r |= (uint32_t)((v >> (3 * b)) & 1ull) << b;
+    return r;
+}
+// key bit order: x in bit 2, y in bit 1, z in bit 0 of every triple
+static uint64_t morton(uint32_t ix, uint32_t iy, uint32_t iz)
+{
+    return (spread3(ix) << 2) | (spread3(iy) << 1) | spread3(iz);
+}
+
+lmfmm_status classify_and_sort(lmfmm_ctx *ctx)
+{
+    const int64_t N = ctx->N;
+    const int L = ctx->med.L;
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int64_t i = 0; i < N; ++i)
+        for (int a = 0; a < 3; ++a) {
+            double v = ctx->xyz[3 * i + a];
+            if (!std::isfinite(v)) {
+                ctx->err = "point " + std::to_string(i) + " has a non-finite coordinate";
+                return LMFMM_ERR_ARG;
+            }
+            lo[a] = std::min(lo[a], v);
+            hi[a] = std::max(hi[a], v);
+        }
+    double ext = 0;
+    for (int a = 0; a < 3; ++a) ext = std::max(ext, hi[a] - lo[a]);
+    double scale = std::max(1.0, ext);
+    ctx->layer.assign(N, 0);
+    for (int64_t i = 0; i < N; ++i) {
+        double z = ctx->xyz[3 * i + 2];
+        int l = 0;
+        for (int j = 0; j < L; ++j) {
+            if (std::fabs(z - ctx->med.d[j]) < 1e-12 * scale) {
+                ctx->err = "point " + std::to_string(i) + " lies on interface " + std::to_string(j);
+                return LMFMM_ERR_ARG;
+            }
+            if (z < ctx->med.d[j]) l = j + 1;
+        }
+        ctx->layer[i] = l;
+    }
+    double h = 0.5 * ext * (1.0 + 1e-9) + 1e-9 * scale;
+    if (h <= 0) h = 1e-3;
+    for (int a = 0; a < 3; ++a) ctx->root_c[a] = 0.5 * (lo[a] + hi[a]);
+    ctx->root_h = h;
+    // depth
+    int D = ctx->prm.depth;
+    if (D < 0) {
+        std::vector<int64_t> cnt(L + 1, 0);
+        for (int64_t i = 0; i < N; ++i) cnt[ctx->layer[i]]++;
+        int64_t nmax = *std::max_element(cnt.begin(), cnt.end());
+        D = 0;
+        int cap = std::max(1, ctx->prm.leaf_cap);
+        while (D < 10 && (double)nmax / std::pow(8.0, D) > cap) ++D;
+    }
+    if (D > 20) D = 20;
+    ctx->depth = D;
+    // keys and sort
+    const double S = 2.0 * h / (double)(1u << D);
+    std::vector<uint64_t> key(N);
+    auto cell = [&](double v, int a) {
+        long c = (long)std::floor((v - (ctx->root_c[a] - h)) / S);
+        long mx = (long)(1u << D) - 1;
+        return (uint32_t)std::min(std::max(c, 0L), mx);
+    };
+    for (int64_t i = 0; i < N; ++i)
+        key[i] = morton(cell(ctx->xyz[3 * i], 0), cell(ctx->xyz[3 * i + 1], 1),
+                        cell(ctx->xyz[3 * i + 2], 2));
+    ctx->perm.resize(N);
+    std::iota(ctx->perm.begin(), ctx->perm.end(), 0);
+    std::sort(ctx->perm.begin(), ctx->perm.end(), [&](int64_t a, int64_t b) {
+        if (ctx->layer[a] != ctx->layer[b]) return ctx->layer[a] < ctx->layer[b];
+        if (key[a] != key[b]) return key[a] < key[b];
+        return a < b;
+    });
+    ctx->sxyz.resize(3 * N);
+    for (int64_t i = 0; i < N; ++i)
+        for (int a = 0; a < 3; ++a) ctx->sxyz[3 * i + a] = ctx->xyz[3 * ctx->perm[i] + a];
+    // tree: per layer, per level
+    ctx->boxes.clear();
+    ctx->lvl0.assign(L + 1, std::vector<int64_t>(D + 1, 0));
+    ctx->lvl1.assign(L + 1, std::vector<int64_t>(D + 1, 0));
+    int64_t p = 0;
+    for (int l = 0; l <= L; ++l) {
+        int64_t q = p;
+        while (q < N && ctx->layer[ctx->perm[q]] == l) ++q;
+        // levels 0..D; boxes of level lev group points by key >> 3(D-lev)
+        for (int lev = 0; lev <= D; ++lev) {
+            ctx->lvl0[l][lev] = (int64_t)ctx->boxes.size();
+            int sh = 3 * (D - lev);
+            int64_t a = p;
+            while (a < q) {
+                uint64_t k = key[ctx->perm[a]] >> sh;
+                int64_t b = a + 1;
+                while (b < q && (key[ctx->perm[b]] >> sh) == k) ++b;
+                Box bx{};
+                bx.key = k;
+                bx.level = lev;
+                bx.layer = l;
+                bx.p0 = a;
+                bx.p1 = b;
+                bx.parent = -1;
+                bx.child0 = -1;
+                bx.nchild = 0;
+                bx.ix = (int)compact3(k >> 2);
+                bx.iy = (int)compact3(k >> 1);
+                bx.iz = (int)compact3(k);
+                double Sl = 2.0 * h / (double)(1u << lev);
+                bx.c[0] = ctx->root_c[0] - h + (bx.ix + 0.5) * Sl;
+                bx.c[1] = ctx->root_c[1] - h + (bx.iy + 0.5) * Sl;
+                bx.c[2] = ctx->root_c[2] - h + (bx.iz + 0.5) * Sl;
+                double r2 = 0;
+                for (int64_t t = a; t < b; ++t) {
+                    double dd = 0;
+                    for (int e = 0; e < 3; ++e) {
+                        double v = ctx->sxyz[3 * t + e] - bx.c[e];
+                        dd += v * v;
+                    }
+                    r2 = std::max(r2, dd);
+                }
+                bx.r = std::sqrt(r2);
+                ctx->boxes.push_back(bx);
+                a = b;
+            }
+            ctx->lvl1[l][lev] = (int64_t)ctx->boxes.size();
+        }
+        // parent/child links
+        for (int lev = 1; lev <= D; ++lev) {
+            int64_t pb = ctx->lvl0[l][lev - 1];
+            for (int64_t b = ctx->lvl0[l][lev]; b < ctx->lvl1[l][lev]; ++b) {
+                while ((ctx->boxes[b].key >> 3) != ctx->boxes[pb].key) ++pb;
+                ctx->boxes[b].parent = pb;
+                if (ctx->boxes[pb].child0 < 0) ctx->boxes[pb].child0 = b;
+                ctx->boxes[pb].nchild++;
+            }
+        }
+        p = q;
+    }
+    return LMFMM_OK;
+}
+
+static double box_min_mapped(const lmfmm_ctx *ctx, const Box &b, const CompDev &c, bool src,
+                             double *mx)
+{
+    double lo = 1e300, hi = -1e300;
+    for (int64_t t = b.p0; t < b.p1; ++t) {
+        double z = ctx->sxyz[3 * t + 2];
+        double zm = src ? comp_src_z(c, z) : comp_tgt_z(c, z);
+        lo = std::min(lo, zm);
+        hi = std::max(hi, zm);
+    }
+    *mx = hi;
+    return lo;
+}
+
+static void box_xy_extent(const lmfmm_ctx *ctx, const Box &b, double lo[2], double hi[2])
+{
+    lo[0] = lo[1] = 1e300;
+    hi[0] = hi[1] = -1e300;
+    for (int64_t t = b.p0; t < b.p1; ++t)
+        for (int e = 0; e < 2; ++e) {
+            lo[e] = std::min(lo[e], ctx->sxyz[3 * t + e]);
+            hi[e] = std::max(hi[e], ctx->sxyz[3 * t + e]);
+        }
+}
+
+lmfmm_status build_host_structures(lmfmm_ctx *ctx)
+{
+    const int L = ctx->med.L;
+    const int D = ctx->depth;
+    const double h = ctx->root_h;
+    std::vector<int64_t> cnt(L + 1, 0);
+    for (int64_t i = 0; i < ctx->N; ++i) cnt[ctx->layer[i]]++;
+    // components
+    ctx->comps.clear();
+    if (L >= 1) {
+        for (int l = 0; l <= L; ++l)
+            for (int lp = 0; lp <= L; ++lp) {
+                if (!cnt[l] || !cnt[lp]) continue;
+                for (int tu = 1; tu >= 0; --tu)
+                    for (int su = 1; su >= 0; --su) {
+                        if (tu && l > L - 1) continue;
+                        if (!tu && l < 1) continue;
+                        if (su && lp < 1) continue;
+                        if (!su && lp > L - 1) continue;
+                        CompDev c{};
+                        c.l = l; c.lp = lp; c.tu = tu; c.su = su;
+                        c.s = comp_sign(l, lp, su);
+                        const double *d = ctx->med.d;
+                        // image of the first slot (eq. equivalent_imag_for_target)
+                        if (tu && su) { c.has_src_refl = !(l < lp); c.refl_src = d[l < L ? l : 0]; }
+                        else if (tu && !su) { c.has_src_refl = !(l <= lp); c.refl_src = d[l < L ? l : 0]; }
+                        else if (!tu && su) { c.has_src_refl = (l < lp); c.refl_src = d[l - 1]; }
+                        else { c.has_src_refl = (l <= lp); c.refl_src = d[l - 1]; }
+                        // effective location of the second slot (eq. equivalent_imag_for_source)
+                        if (!su) { c.has_tgt_refl = (l <= lp); c.refl_tgt = d[lp < L ? lp : 0]; }
+                        else { c.has_tgt_refl = !(l < lp); c.refl_tgt = d[lp >= 1 ? lp - 1 : 0]; }
+                        if (!c.has_src_refl) c.refl_src = 0;
+                        if (!c.has_tgt_refl) c.refl_tgt = 0;
+                        ctx->comps.push_back(c);
+                    }
+            }
+    }
+    // dual-tree traversal
+    const double theta = ctx->prm.theta, eta = ctx->prm.eta;
+    struct PairRec { int comp, level; int64_t src, tgt; };
+    std::vector<PairRec> far;
+    ctx->near.clear();
+    ctx->n_near_pp = 0;
+    std::vector<std::pair<int64_t, int64_t>> stack;
+    for (int ci = 0; ci < (int)ctx->comps.size(); ++ci) {
+        const CompDev &c = ctx->comps[ci];
+        stack.clear();
+        stack.push_back({ctx->lvl0[c.l][0], ctx->lvl0[c.lp][0]});
+        while (!stack.empty()) {
+            auto [bs, bt] = stack.back();
+            stack.pop_back();
+            const Box &B = ctx->boxes[bs], &C = ctx->boxes[bt];
+            double zs = comp_src_z(c, B.c[2]), zt = comp_tgt_z(c, C.c[2]);
+            double dx = B.c[0] - C.c[0], dy = B.c[1] - C.c[1], dz = zs - zt;
+            double R = std::sqrt(dx * dx + dy * dy + dz * dz);
+            double vz = c.s * dz;
+            bool adm = (B.r + C.r <= theta * R) && (vz >= eta * R) && (vz > 0);
+            if (adm) {
+                far.push_back({ci, B.level, bs, bt});
+            } else if (B.level == D) {
+                NearPair np{};
+                np.comp = ci;
+                np.src = bs;
+                np.tgt = bt;
+                np.coef0 = ctx->n_near_pp;
+                double smx, tmx;
+                double smn = box_min_mapped(ctx, B, c, true, &smx);
+                double tmn = box_min_mapped(ctx, C, c, false, &tmx);
+                np.dzmin = c.s > 0 ? smn - tmx : tmn - smx;
+                if (!(np.dzmin > 0)) {
+                    ctx->err = "internal: image and effective points not separated";
+                    return LMFMM_ERR_ARG;
+                }
+                double blo[2], bhi[2], clo[2], chi[2];
+                box_xy_extent(ctx, B, blo, bhi);
+                box_xy_extent(ctx, C, clo, chi);
+                double mx = std::max(std::fabs(bhi[0] - clo[0]), std::fabs(chi[0] - blo[0]));
+                double my = std::max(std::fabs(bhi[1] - clo[1]), std::fabs(chi[1] - blo[1]));
+                np.rhomax = std::sqrt(mx * mx + my * my);
+                ctx->n_near_pp += (B.p1 - B.p0) * (C.p1 - C.p0);
+                ctx->near.push_back(np);
+            } else {
+                for (int i = 0; i < B.nchild; ++i)
+                    for (int j = 0; j < C.nchild; ++j)
+                        stack.push_back({B.child0 + i, C.child0 + j});
+            }
+        }
+    }
+    // geometry deduplication: (comp, level, dx^2+dy^2 in cells, iz_s, iz_t)
+    std::map<std::tuple<int, int, int64_t, int, int>, int> gid;
+    std::vector<int> pg(far.size());
+    ctx->geoms.clear();
+    for (size_t i = 0; i < far.size(); ++i) {
+        const Box &B = ctx->boxes[far[i].src], &C = ctx->boxes[far[i].tgt];
+        int64_t ddx = B.ix - C.ix, ddy = B.iy - C.iy;
+        auto key = std::make_tuple(far[i].comp, far[i].level, ddx * ddx + ddy * ddy, B.iz, C.iz);
+        auto it = gid.find(key);
+        if (it == gid.end()) {
+            Geom g{};
+            g.comp = far[i].comp;
+            g.level = far[i].level;
+            double Sl = 2.0 * h / (double)(1u << g.level);
+            g.rho = Sl * std::sqrt((double)(ddx * ddx + ddy * ddy));
+            const CompDev &c = ctx->comps[g.comp];
+            g.zs = comp_src_z(c, B.c[2]);
+            g.zt = comp_tgt_z(c, C.c[2]);
+            it = gid.emplace(key, (int)ctx->geoms.size()).first;
+            ctx->geoms.push_back(g);
+        }
+        pg[i] = it->second;
+    }
+    std::vector<int64_t> off(ctx->geoms.size() + 1, 0);
+    for (size_t i = 0; i < far.size(); ++i) off[pg[i] + 1]++;
+    for (size_t g = 0; g < ctx->geoms.size(); ++g) off[g + 1] += off[g];
+    ctx->m2l.assign(far.size(), M2LPair{});
+    std::vector<int64_t> pos(off.begin(), off.end() - 1);
+    for (size_t i = 0; i < far.size(); ++i) {
+        const Box &B = ctx->boxes[far[i].src], &C = ctx->boxes[far[i].tgt];
+        double dx = B.c[0] - C.c[0], dy = B.c[1] - C.c[1];
+        double rr = std::sqrt(dx * dx + dy * dy);
+        M2LPair mp{far[i].src, far[i].tgt, rr > 0 ? dx / rr : 1.0, rr > 0 ? dy / rr : 0.0};
+        ctx->m2l[pos[pg[i]]++] = mp;
+    }
+    for (size_t g = 0; g < ctx->geoms.size(); ++g) {
+        ctx->geoms[g].pair0 = off[g];
+        ctx->geoms[g].pair1 = off[g + 1];
+    }
+    // translation groups (child level lev, octant from the child's key)
+    ctx->tgroups.clear();
+    ctx->tpair_child.clear();
+    ctx->tpair_parent.clear();
+    for (int l = 0; l <= L; ++l) {
+        if (!cnt[l]) continue;
+        for (int lev = 1; lev <= D; ++lev) {
+            std::vector<int64_t> byoct[8];
+            for (int64_t b = ctx->lvl0[l][lev]; b < ctx->lvl1[l][lev]; ++b)
+                byoct[ctx->boxes[b].key & 7].push_back(b);
+            double Sc = 2.0 * h / (double)(1u << lev);
+            for (int o = 0; o < 8; ++o) {
+                if (byoct[o].empty()) continue;
+                TransGroup g{};
+                g.layer = l;
+                g.level = lev;
+                g.octant = o;
+                g.t[0] = ((o >> 2) & 1 ? 0.5 : -0.5) * Sc;
+                g.t[1] = ((o >> 1) & 1 ? 0.5 : -0.5) * Sc;
+                g.t[2] = (o & 1 ? 0.5 : -0.5) * Sc;
+                g.pair0 = (int64_t)ctx->tpair_child.size();
+                for (int64_t b : byoct[o]) {
+                    ctx->tpair_child.push_back(b);
+                    ctx->tpair_parent.push_back(ctx->boxes[b].parent);
+                }
+                g.pair1 = (int64_t)ctx->tpair_child.size();
+                ctx->tgroups.push_back(g);
+            }
+        }
+    }
+    return LMFMM_OK;
+}
+
+// ---------------------------------------------------------------- Chebyshev
+
+typedef long double ld;
+typedef std::complex<long double> lz;
+
+// K_n of Appendix B for (n, m >= 0)
+static int cheb_K(int n, int m)
+{
+    if (n % 2 == 0) return n / 2;
+    return (m % 2 == 0) ? (n + 1) / 2 : (n - 1) / 2;
+}
+
+// normalised P^_n^m(cos t), 0 <= m <= n <= p, long double
+void legendre_ld(int p, ld x, ld s, std::vector<ld> &P)
+{
+    P.assign((p + 1) * (p + 2) / 2, 0);
+    ld pmm = 1.0L / std::sqrt(4.0L * 3.14159265358979323846264338327950288L);
+    for (int m = 0; m <= p; ++m) {
+        if (m > 0) pmm = -pmm * s * std::sqrt((ld)(2 * m + 1) / (ld)(2 * m));
+        P[tidx(m, m)] = pmm;
+        if (m == p) break;
+        ld p1 = std::sqrt((ld)(2 * m + 3)) * x * pmm;
+        P[tidx(m + 1, m)] = p1;
+        ld p0 = pmm;
+        for (int n = m + 2; n <= p; ++n) {
+            ld a = std::sqrt((ld)(4 * n * n - 1) / (ld)(n * n - m * m));
+            ld b = std::sqrt((ld)((n - 1) * (n - 1) - m * m) / (ld)(4 * (n - 1) * (n - 1) - 1));
+            ld p2 = a * (x * p1 - b * p0);
+            P[tidx(n, m)] = p2;
+            p0 = p1;
+            p1 = p2;
+        }
+    }
+}
+
+// B^k_{n,m} (Appendix B): Chebyshev coefficients in T_k(cos 2 theta) of the
+// polynomial P^_n^m(cos theta) / tau_{nm}(theta), obtained exactly by
+// interpolation at K_n + 1 Chebyshev points (the printed backward recursion
+// has an inconsistent n = 0 case; interpolation reproduces it elsewhere).
+void bcoef_table(int p, int KMAX, std::vector<double> &B)
+{
+    const ld PI = 3.14159265358979323846264338327950288L;
+    int T = (p + 1) * (p + 2) / 2;
+    B.assign((size_t)T * (KMAX + 1), 0.0);
+    std::vector<ld> P;
+    for (int n = 0; n <= p; ++n)
+        for (int m = 0; m <= n; ++m) {
+            int K = cheb_K(n, m);
+            std::vector<ld> f(K + 1), xs(K + 1);
+            for (int j = 0; j <= K; ++j) {
+                ld x = std::cos(PI * (j + 0.5L) / (K + 1));
+                ld ct = std::sqrt((1 + x) / 2), st = std::sqrt((1 - x) / 2);
+                legendre_ld(p, ct, st, P);
+                ld tau = 1;
+                if (n % 2 == 1 && m % 2 == 0) tau = 1 / ct;
+                else if (n % 2 == 1 && m % 2 == 1) tau = st;
+                else if (n % 2 == 0 && m % 2 == 1) tau = st / ct;
+                f[j] = P[tidx(n, m)] / tau;
+                xs[j] = x;
+            }
+            for (int k = 0; k <= K; ++k) {
+                ld s = 0;
+                for (int j = 0; j <= K; ++j) s += f[j] * std::cos(k * std::acos(xs[j]));
+                s *= 2.0L / (K + 1);
+                if (k == 0) s /= 2;
+                B[(size_t)tidx(n, m) * (KMAX + 1) + k] = (double)s;
+            }
+        }
+}
+
+// C^{ab}_{js} (Appendix A): T_j(a x + b) = sum_s C_js T_s(x), by the
+// three-term recurrence T_{j+1}(y) = 2 y T_j(y) - T_{j-1}(y) with
+// x T_s = (T_{s+1} + T_{|s-1|}) / 2 in the Chebyshev basis.
+static void ccoef(lz a, lz b, int J, std::vector<std::vector<lz>> &C)
+{
+    C.assign(J + 1, std::vector<lz>(J + 2, 0));
+    C[0][0] = 1;
+    if (J >= 1) { C[1][0] = b; C[1][1] = a; }
+    for (int j = 1; j < J; ++j) {
+        std::vector<lz> xT(J + 2, 0);
+        for (int s = 0; s <= j; ++s) {
+            if (C[j][s] == lz(0)) continue;
+            xT[s + 1] += C[j][s] * 0.5L;
+            xT[s == 0 ? 1 : s - 1] += C[j][s] * 0.5L;
+        }
+        for (int s = 0; s <= j + 1; ++s)
+            C[j + 1][s] = 2.0L * (a * xT[s] + b * C[j][s]) - (s <= j - 1 ? C[j - 1][s] : lz(0));
+    }
+}
+
+// G tensor of one (k, k') pair: G[(n',|m'|)][(nu,|mu|)][l], the coefficients of
+// P^_{n'}^{m'}(cos b) P^_nu^mu(cos b') / (s_{m'mu} tau tau') in T_l(cos 2 b0),
+// b0 the angle of the smaller |k| (eqs. legendre_Q_v, legendre_Q_w with the
+// product T_i T_s = (T_{i+s} + T_{|i-s|})/2).
+void gtensor(int p, const std::vector<double> &Bcoef, int KM, zc k_, zc kp_, cd *dst0)
+{
+    const int T = (p + 1) * (p + 2) / 2, LM = p + 2;
+    lz k(k_.real(), k_.imag()), kp(kp_.real(), kp_.imag());
+    bool src_primary = std::abs(k) <= std::abs(kp);
+    lz a = src_primary ? (k / kp) * (k / kp) : (kp / k) * (kp / k);
+    lz b = 1.0L - a;
+    std::vector<std::vector<lz>> C;
+    ccoef(a, b, KM, C);
+    for (int n1 = 0; n1 <= p; ++n1)
+        for (int m1 = 0; m1 <= n1; ++m1)
+            for (int nu = 0; nu <= p; ++nu)
+                for (int mu = 0; mu <= nu; ++mu) {
+                    const double *Bs = &Bcoef[(size_t)tidx(n1, m1) * (KM + 1)];
+                    const double *Bt = &Bcoef[(size_t)tidx(nu, mu) * (KM + 1)];
+                    int Ks = cheb_K(n1, m1), Kt = cheb_K(nu, mu);
+                    std::vector<lz> G(LM, 0);
+                    int Kp = src_primary ? Ks : Kt, Kq = src_primary ? Kt : Ks;
+                    const double *Bp = src_primary ? Bs : Bt, *Bq = src_primary ? Bt : Bs;
+                    for (int i = 0; i <= Kp; ++i)
+                        for (int j = 0; j <= Kq; ++j) {
+                            lz w = (ld)Bp[i] * (ld)Bq[j] * 0.5L;
+                            for (int s = 0; s <= j; ++s) {
+                                lz v = w * C[j][s];
+                                G[i + s] += v;
+                                G[i > s ? i - s : s - i] += v;
+                            }
+                        }
+                    cd *dst = dst0 + ((size_t)tidx(n1, m1) * T + tidx(nu, mu)) * LM;
+                    for (int q = 0; q < LM; ++q) dst[q] = cd{(double)G[q].real(), (double)G[q].imag()};
+                }
+}
+
+void chebyshev_tables(lmfmm_ctx *ctx)
+{
+    const int p = ctx->prm.p;
+    ctx->KMAX = (p + 1) / 2;
+    bcoef_table(p, ctx->KMAX, ctx->Bcoef);
+    const int T = (p + 1) * (p + 2) / 2;
+    ctx->LMAXC = p + 2;
+    const int LM = ctx->LMAXC, KM = ctx->KMAX;
+    std::map<std::pair<int, int>, int> seen;
+    ctx->comp_gidx.assign(ctx->comps.size(), 0);
+    ctx->Gten.clear();
+    for (size_t ci = 0; ci < ctx->comps.size(); ++ci) {
+        int l = ctx->comps[ci].l, lp = ctx->comps[ci].lp;
+        auto key = std::make_pair(l, lp);
+        auto it = seen.find(key);
+        if (it != seen.end()) { ctx->comp_gidx[ci] = it->second; continue; }
+        int gi = (int)seen.size();
+        seen[key] = gi;
+        ctx->comp_gidx[ci] = gi;
+        size_t base = ctx->Gten.size();
+        ctx->Gten.resize(base + (size_t)T * T * LM, cd{0, 0});
+        gtensor(p, ctx->Bcoef, KM, zc(ctx->med.k[l].x, ctx->med.k[l].y),
+                zc(ctx->med.k[lp].x, ctx->med.k[lp].y), &ctx->Gten[base]);
+    }
+}
+
+}  // namespace lmf
+
+namespace lmf {
+
+// ------------------------------------------------- translation matrices
+// M2M and L2L of Section 2 (eqs. maxwell_M2M_freespace, maxwell_L2L_freespace)
+// act on the regular expansions of the reaction field.  Writing the ME as the
+// spherical-harmonic coefficients of the far-field pattern
+// F(K) = sum_j q_j e^{i k K.(r_j - c)} = sum M_nm i^n Y_nm(K), a shift of
+// centre by t multiplies F by e^{i k K.t}; with the plane-wave expansion
+// e^{i k K.t} = 4 pi sum_l i^l j_l(k|t|) sum_mu Y_l^mu(K) conj(Y_l^mu(t^)),
+//   W_{nm,n'm'}(t) = int e^{ikK.t} Y_n'm' conj(Y_nm) dOmega
+//                  = 4 pi sum_l i^l j_l(k|t|) conj(Y_l^{m-m'}(t^)) G(l, n', n),
+// G = int Y_l^{m-m'} Y_n'^m' conj(Y_n^m) (Gaunt coefficients, exact by
+// Gauss-Legendre quadrature of a polynomial).  Every entry is then accurate
+// relative to its own size, which matters because M2L multiplies high orders
+// by large factors.  M2M = i^(n'-n) W(t), L2L = i^(n-n') W(t), t = child - parent.
+
+// P~_n^m(x) = (m<0 ? (-1)^m : 1) P^_n^|m|(x)
+static ld ptilde(const std::vector<ld> &P, int n, int m)
+{
+    int am = m < 0 ? -m : m;
+    ld v = P[tidx(n, am)];
+    return (m < 0 && (am & 1)) ? -v : v;
+}
+
+void gaunt_table(int p, std::vector<int64_t> &off, std::vector<int> &lval, std::vector<double> &gval)
+{
+    const int P = (p + 1) * (p + 1);
+    const int nq = 2 * p + 4;
+    const int lmax = 2 * p;
+    // Gauss-Legendre nodes (long double Newton)
+    std::vector<ld> xq(nq), wq(nq);
+    for (int i = 0; i < nq; ++i) {
+        ld x = std::cos(3.14159265358979323846264338327950288L * (i + 0.75L) / (nq + 0.5L)), dp = 0;
+        for (int it = 0; it < 100; ++it) {
+            ld p0 = 1, p1 = x;
+            for (int n = 2; n <= nq; ++n) {
+                ld p2 = ((2 * n - 1) * x * p1 - (n - 1) * p0) / n;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = nq * (x * p1 - p0) / (x * x - 1);
+            ld dx = p1 / dp;
+            x -= dx;
+            if (std::fabs((double)dx) < 1e-22) break;
+        }
+        xq[i] = x;
+        wq[i] = 2.0L / ((1 - x * x) * dp * dp);
+    }
+    std::vector<std::vector<ld>> Pq(nq);
+    for (int q = 0; q < nq; ++q) legendre_ld(lmax, xq[q], std::sqrt(1 - xq[q] * xq[q]), Pq[q]);
+    const ld twopi = 2 * 3.14159265358979323846264338327950288L;
+    off.assign((size_t)P * P + 1, 0);
+    lval.clear();
+    gval.clear();
+    for (int n = 0; n <= p; ++n)
+        for (int m = -n; m <= n; ++m)
+            for (int n1 = 0; n1 <= p; ++n1)
+                for (int m1 = -n1; m1 <= n1; ++m1) {
+                    int mu = m - m1;
+                    int amu = mu < 0 ? -mu : mu;
+                    for (int l = std::abs(n - n1); l <= n + n1; ++l) {
+                        if ((l + n + n1) & 1) continue;
+                        if (l < amu) continue;
+                        ld s = 0;
+                        for (int q = 0; q < nq; ++q)
+                            s += wq[q] * ptilde(Pq[q], l, mu) * ptilde(Pq[q], n1, m1) * ptilde(Pq[q], n, m);
+                        s *= twopi;
+                        if (std::fabs((double)s) < 1e-30) continue;
+                        lval.push_back(l);
+                        gval.push_back((double)s);
+                    }
+                    off[(size_t)nidx(n, m) * P + nidx(n1, m1) + 1] = (int64_t)lval.size();
+                }
+}
+
+// spherical Bessel j_0..j_L at complex z (long double Miller recurrence,
+// normalised against j_0 or j_1, whichever is larger)
+static void sph_bessel_ld(lz z, int L, std::vector<lz> &j)
+{
+    j.assign(L + 1, 0);
+    ld az = std::abs(z);
+    if (az < 1e-18L) {
+        j[0] = 1;
+        return;
+    }
+    int N = L + 30 + (int)(1.5L * az);
+    lz fnp1 = 0, fn = 1e-30L, f1 = 0;
+    for (int k = N; k >= 1; --k) {
+        if (k <= L) j[k] = fn;
+        if (k == 1) f1 = fn;
+        lz fkm1 = (ld)(2 * k + 1) / z * fn - fnp1;
+        fnp1 = fn;
+        fn = fkm1;
+        if (std::abs(fn) > 1e300L) {
+            fn *= 1e-300L;
+            fnp1 *= 1e-300L;
+            f1 *= 1e-300L;
+            for (int q = k; q <= L; ++q) j[q] *= 1e-300L;
+        }
+    }
+    j[0] = fn;
+    lz j0 = std::sin(z) / z, j1 = std::sin(z) / (z * z) - std::cos(z) / z;
+    lz sc = std::abs(j0) >= std::abs(j1) ? j0 / fn : j1 / f1;
+    for (auto &v : j) v *= sc;
+}
+
+void translation_matrix(int p, zc kk, const double t[3], const std::vector<int64_t> &off,
+                        const std::vector<int> &lval, const std::vector<double> &gval, cd *up,
+                        cd *dn)
+{
+    const int P = (p + 1) * (p + 1);
+    const int lmax = 2 * p;
+    ld tn = std::sqrt((ld)t[0] * t[0] + (ld)t[1] * t[1] + (ld)t[2] * t[2]);
+    std::vector<lz> jl;
+    sph_bessel_ld(lz(kk.real(), kk.imag()) * tn, lmax, jl);
+    std::vector<ld> Pt;
+    ld ct = tn > 0 ? t[2] / tn : 1, st = tn > 0 ? std::sqrt((ld)t[0] * t[0] + (ld)t[1] * t[1]) / tn : 0;
+    legendre_ld(lmax, ct, st, Pt);
+    ld phi = std::atan2((ld)t[1], (ld)t[0]);
+    const ld fourpi = 4 * 3.14159265358979323846264338327950288L;
+    for (int n = 0; n <= p; ++n)
+        for (int m = -n; m <= n; ++m)
+            for (int n1 = 0; n1 <= p; ++n1)
+                for (int m1 = -n1; m1 <= n1; ++m1) {
+                    size_t e = (size_t)nidx(n, m) * P + nidx(n1, m1);
+                    int mu = m - m1;
+                    // conj(Y_l^mu(t^)) = P~_l^mu e^{-i mu phi}
+                    lz eph = std::polar((ld)1, -(ld)mu * phi);
+                    lz s = 0;
+                    for (int64_t q = off[e]; q < off[e + 1]; ++q) {
+                        int l = lval[q];
+                        lz il = (l % 4 == 0) ? lz(1) : (l % 4 == 1) ? lz(0, 1) : (l % 4 == 2) ? lz(-1) : lz(0, -1);
+                        s += il * jl[l] * ptilde(Pt, l, mu) * (ld)gval[q];
+                    }
+                    s *= fourpi * eph;
+                    int d = n1 - n;
+                    auto ip = [](int k) {
+                        k = ((k % 4) + 4) % 4;
+                        return k == 0 ? lz(1) : k == 1 ? lz(0, 1) : k == 2 ? lz(-1) : lz(0, -1);
+                    };
+                    lz u = ip(d) * s, v = ip(-d) * s;
+                    up[e] = cd{(double)u.real(), (double)u.imag()};
+                    dn[e] = cd{(double)v.real(), (double)v.imag()};
+                }
+}
+
+}  // namespace lmf

@@ -1,0 +1,87 @@
+// Device-side records and kernel launchers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "gauss.cuh"
+#include "internal.h"
+
+#define LMF_PMAX 20
+
+namespace lmf {
+
+// k_rho nodes of one Sommerfeld integral (Section 3.5):
+//   [0, n1)                Gamma_1 from 0 to a (Gauss-Legendre 16 per panel)
+//   [n1, n1+nmid)          real segment [a, x1] with J_d (Gauss-Legendre 8)
+//   then, when nray > 0, the rays Gamma_2+ and Gamma_2- from x1,
+//   k = x1 + t (dz +- i rho)/r, t in [0, tend], with H^(1)_d/2 and H^(2)_d/2.
+struct QuadPlanDev {
+    int n1, nmid, nray, pad;
+    double a, kp, x1;   // Gamma_1 end, its shape parameter, end of the real segment
+    double cr, sr, tend;// ray direction (dz/r, rho/r) and length
+};
+
+struct GeomDev {
+    int comp, src_primary;
+    double rho, zs, zt;
+    QuadPlanDev plan;
+    int64_t node0;      // first node within its tabulation batch
+    int64_t stride;     // node count of its batch (factor-array stride)
+    int64_t tab_index;  // table slot
+    int batch, pad;
+};
+
+struct TransGroupDev {
+    int layer, level;
+    double t[3];
+};
+
+struct BoxDev {
+    int64_t p0, p1;
+    double c[3];
+    int layer, pad;
+};
+
+struct GemmWork {       // M2M / L2L: pairs [pair0, pair0 + npair) of one translation group
+    int group, npair;
+    int64_t pair0;
+};
+
+struct M2LWork {        // one M2L table applied to a chunk of pairs of one geometry
+    int geom, t, npair, pad;
+    int64_t pair0;
+};
+
+// k_tab.cu
+void launch_densities(const MediumDev &M, int l, int lp, int64_t n, const cd *kr, cd *out,
+                      cudaStream_t st);
+void launch_tab_batch(const GeomDev *dG, int g0, int nb, int qmax, const MediumDev &M,
+                      const CompDev *dcomps, int p, const cd *dGten, const int *dcgidx,
+                      cd *scratch, int64_t stride, cd *tab, int *dflag, cudaStream_t st);
+
+// k_fmm.cu
+cudaError_t configure_fmm_kernels();
+cudaError_t configure_tab_kernels();
+void launch_gather_in(int64_t N, const int64_t *perm, const cd *J, cd *qh, bool conj_in,
+                      cudaStream_t st);
+void launch_scatter_out(int64_t N, const int64_t *perm, const cd *phih, cd *Phi, bool conj_out,
+                        cudaStream_t st);
+void launch_p2m(int p, int64_t nleaf, const int64_t *leaves, const BoxDev *boxes,
+                const double *xyz, const cd *qh, const MediumDev &M, cd *me, cudaStream_t st);
+void launch_l2p(int p, int64_t nleaf, const int64_t *leaves, const BoxDev *boxes,
+                const double *xyz, const cd *le, const MediumDev &M, cd *phih, cudaStream_t st);
+void launch_group_gemm(int p, int64_t nwork, const GemmWork *work, const cd *mats,
+                       const int64_t *src, const int64_t *dst, const cd *in, cd *out,
+                       bool atomic, cudaStream_t st);
+void launch_m2l(int p, int64_t nwork, const M2LWork *work, const GeomDev *geoms,
+                const CompDev *comps, const M2LPair *pairs, const cd *tab, const cd *me, cd *le,
+                cudaStream_t st);
+void launch_s2t_pre(int64_t nnear, const NearPair *near, const BoxDev *boxes, const double *xyz,
+                    const MediumDev &M, const CompDev *comps, double a, double kp, cd *coef,
+                    int *dflag, cudaStream_t st);
+void launch_s2t_apply(int64_t nnear, const NearPair *near, const BoxDev *boxes,
+                      const double *xyz, const cd *coef, const cd *qh, cd *phih,
+                      cudaStream_t st);
+
+}  // namespace lmf

@@ -1,0 +1,270 @@
+"""Thin ctypes binding of the lmfmm C ABI (include/lmfmm.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Device buffers are torch tensors (complex128, contiguous); streams
+are torch CUDA streams.  Importing this module does not build anything; if
+the compiled library is missing it raises, so no silent fallback exists.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_STATE, ERR_QUAD, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+FP64, MIXED = 0, 1
+
+
+class C128(ctypes.Structure):
+    _fields_ = [("re", ctypes.c_double), ("im", ctypes.c_double)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int), ("depth", ctypes.c_int), ("leaf_cap", ctypes.c_int),
+                ("theta", ctypes.c_double), ("eta", ctypes.c_double),
+                ("quad_tol", ctypes.c_double), ("precision", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n_points", ctypes.c_int64), ("n_layers", ctypes.c_int),
+                ("n_components", ctypes.c_int), ("depth", ctypes.c_int),
+                ("n_boxes", ctypes.c_int64), ("n_m2l_pairs", ctypes.c_int64),
+                ("n_geometries", ctypes.c_int64), ("n_near_pairs", ctypes.c_int64),
+                ("n_near_point_pairs", ctypes.c_int64), ("n_quad_nodes", ctypes.c_int64),
+                ("bytes_tables", ctypes.c_double), ("ms_setup", ctypes.c_double),
+                ("ms_stage", ctypes.c_double * 8), ("m2l_columns", ctypes.c_int64)]
+
+
+EXPORTS = ["lmfmm_default_params", "lmfmm_create", "lmfmm_set_layers", "lmfmm_set_points",
+           "lmfmm_build", "lmfmm_matvec", "lmfmm_matvec_host", "lmfmm_matvec_adjoint",
+           "lmfmm_direct", "lmfmm_densities", "lmfmm_m2l_table", "lmfmm_translation_matrix",
+           "lmfmm_get_stats", "lmfmm_last_error", "lmfmm_destroy"]
+
+
+class LmfmmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("lmfmm error %d: %s" % (code, msg))
+        self.code = code
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load the compiled library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError("liblmfmm.so is not built (run paper_2507_18491_gb300.build.build())")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    i, i64, d = ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    sig = {
+        "lmfmm_default_params": [ctypes.POINTER(Params)],
+        "lmfmm_create": [ctypes.POINTER(P), ctypes.POINTER(Params), i],
+        "lmfmm_set_layers": [P, i, ctypes.POINTER(d), ctypes.POINTER(C128)],
+        "lmfmm_set_points": [P, i64, ctypes.POINTER(d)],
+        "lmfmm_build": [P, P],
+        "lmfmm_matvec": [P, P, P, P],
+        "lmfmm_matvec_host": [P, P, P, P],
+        "lmfmm_matvec_adjoint": [P, P, P, P],
+        "lmfmm_direct": [P, P, P, P],
+        "lmfmm_densities": [P, i, i, i64, P, P, P],
+        "lmfmm_m2l_table": [P, i, i, i, i, d, d, d, P, P],
+        "lmfmm_translation_matrix": [i, C128, ctypes.POINTER(d), P, P],
+        "lmfmm_get_stats": [P, ctypes.POINTER(Stats)],
+        "lmfmm_last_error": [P],
+        "lmfmm_destroy": [P],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.lmfmm_last_error.restype = ctypes.c_char_p
+    lib.lmfmm_destroy.restype = None
+    _lib = lib
+    return lib
+
+
+def _check(rc, ctx=None):
+    if rc != OK:
+        msg = load().lmfmm_last_error(ctx)
+        raise LmfmmError(rc, msg.decode() if msg else "")
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t, n3=None):
+    import torch
+    if not (t.is_cuda and t.dtype == torch.complex128 and t.is_contiguous()):
+        raise ValueError("expected a contiguous complex128 CUDA tensor")
+    if n3 is not None and tuple(t.shape) != (n3, 3):
+        raise ValueError("expected shape (%d, 3), got %s" % (n3, tuple(t.shape)))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ------------------------------------------------------------ C-ABI mirror
+def default_params() -> Params:
+    prm = Params()
+    _check(load().lmfmm_default_params(ctypes.byref(prm)))
+    return prm
+
+
+def create(prm: Params, device: int = 0):
+    h = ctypes.c_void_p()
+    _check(load().lmfmm_create(ctypes.byref(h), ctypes.byref(prm), int(device)))
+    return h
+
+
+def set_layers(ctx, d, k):
+    d = np.ascontiguousarray(np.asarray(d, np.float64).reshape(-1))
+    k = np.asarray(k, np.complex128).reshape(-1)
+    karr = (C128 * k.size)(*[C128(float(v.real), float(v.imag)) for v in k])
+    _check(load().lmfmm_set_layers(ctx, int(d.size), d.ctypes.data_as(ctypes.POINTER(
+        ctypes.c_double)), karr), ctx)
+
+
+def set_points(ctx, xyz):
+    xyz = np.ascontiguousarray(np.asarray(xyz, np.float64).reshape(-1, 3))
+    _check(load().lmfmm_set_points(ctx, int(xyz.shape[0]),
+                                   xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), ctx)
+
+
+def build(ctx, stream=None):
+    _check(load().lmfmm_build(ctx, _stream(stream)), ctx)
+
+
+def matvec(ctx, J, Phi, stream=None):
+    _check(load().lmfmm_matvec(ctx, _dptr(J), _dptr(Phi), _stream(stream)), ctx)
+
+
+def matvec_adjoint(ctx, y, Phi, stream=None):
+    _check(load().lmfmm_matvec_adjoint(ctx, _dptr(y), _dptr(Phi), _stream(stream)), ctx)
+
+
+def matvec_host(ctx, J: np.ndarray, Phi: np.ndarray, stream=None):
+    for a in (J, Phi):
+        if a.dtype != np.complex128 or not a.flags.c_contiguous:
+            raise ValueError("expected contiguous complex128 arrays")
+    _check(load().lmfmm_matvec_host(ctx, ctypes.c_void_p(J.ctypes.data),
+                                    ctypes.c_void_p(Phi.ctypes.data), _stream(stream)), ctx)
+
+
+def direct(ctx, J, Phi, stream=None):
+    _check(load().lmfmm_direct(ctx, _dptr(J), _dptr(Phi), _stream(stream)), ctx)
+
+
+def densities(ctx, l, lp, krho, out, stream=None):
+    _check(load().lmfmm_densities(ctx, int(l), int(lp), int(krho.numel()), _dptr(krho),
+                                  _dptr(out), _stream(stream)), ctx)
+
+
+def m2l_table(ctx, l, lp, tgt_up, src_up, rho, zs, zt, out, stream=None):
+    _check(load().lmfmm_m2l_table(ctx, int(l), int(lp), int(tgt_up), int(src_up), float(rho),
+                                  float(zs), float(zt), _dptr(out), _stream(stream)), ctx)
+
+
+def translation_matrix(p, k, t):
+    """(M2M, L2L) matrices [P, P] (numpy complex128) for wavenumber k and
+    shift t = child centre - parent centre.  Host only."""
+    P = (p + 1) ** 2
+    up = np.zeros((P, P), np.complex128)
+    dn = np.zeros((P, P), np.complex128)
+    t = np.ascontiguousarray(np.asarray(t, np.float64))
+    _check(load().lmfmm_translation_matrix(int(p), C128(float(np.real(k)), float(np.imag(k))),
+                                           t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                           ctypes.c_void_p(up.ctypes.data),
+                                           ctypes.c_void_p(dn.ctypes.data)))
+    return up, dn
+
+
+def get_stats(ctx) -> dict:
+    s = Stats()
+    _check(load().lmfmm_get_stats(ctx, ctypes.byref(s)), ctx)
+    out = {f: getattr(s, f) for f, _ in Stats._fields_ if f != "ms_stage"}
+    names = ["p2m", "m2m", "m2l", "l2l", "l2p", "s2t", "permute", "total"]
+    out["ms_stage"] = {n: s.ms_stage[i] for i, n in enumerate(names)}
+    return out
+
+
+def last_error(ctx=None) -> str:
+    m = load().lmfmm_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def destroy(ctx):
+    if ctx:
+        load().lmfmm_destroy(ctx)
+
+
+# ------------------------------------------------------------- convenience
+class Operator:
+    """The reaction-field operator of one point set in one layered medium.
+
+    ``Operator(d, k, xyz, p=...)`` sets up the context; ``build()`` runs the
+    setup on the GPU; ``matvec(J)`` returns A J (torch complex128, [N,3])."""
+
+    def __init__(self, d, k, xyz, p=8, depth=-1, leaf_cap=64, theta=0.55, eta=0.1,
+                 precision=FP64, device=0):
+        prm = default_params()
+        prm.p, prm.depth, prm.leaf_cap = int(p), int(depth), int(leaf_cap)
+        prm.theta, prm.eta, prm.precision = float(theta), float(eta), int(precision)
+        self.ctx = create(prm, device)
+        self.N = int(np.asarray(xyz).shape[0])
+        self.device = device
+        set_layers(self.ctx, d, k)
+        set_points(self.ctx, xyz)
+
+    def build(self, stream=None):
+        build(self.ctx, stream)
+        return self
+
+    def matvec(self, J, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty_like(J)
+        matvec(self.ctx, J, out, stream)
+        return out
+
+    def rmatvec(self, y, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty_like(y)
+        matvec_adjoint(self.ctx, y, out, stream)
+        return out
+
+    def direct(self, J, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty_like(J)
+        direct(self.ctx, J, out, stream)
+        return out
+
+    def stats(self):
+        return get_stats(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

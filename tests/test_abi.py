@@ -1,0 +1,49 @@
+"""The C-ABI library loads and exports every symbol include/lmfmm.h declares;
+argument validation that needs no GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2507_18491_gb300 import build, lmfmm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "lmfmm.h")).read()
+    return sorted(set(re.findall(r"\b(lmfmm_[a-z_0-9]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return lmfmm.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(lmfmm.EXPORTS)
+
+
+def test_default_params(lib):
+    prm = lmfmm.default_params()
+    assert prm.p == 8 and prm.depth == -1 and prm.precision == lmfmm.FP64
+    assert 0 < prm.theta < 1
+
+
+def test_bad_params_rejected_before_device_use(lib):
+    prm = lmfmm.default_params()
+    prm.p = 0
+    h = ctypes.c_void_p()
+    rc = lib.lmfmm_create(ctypes.byref(h), ctypes.byref(prm), 0)
+    assert rc == lmfmm.ERR_ARG
+    assert b"parameter" in lib.lmfmm_last_error(None)
+    prm = lmfmm.default_params()
+    prm.theta = 1.5
+    assert lib.lmfmm_create(ctypes.byref(h), ctypes.byref(prm), 0) == lmfmm.ERR_ARG
+    assert lib.lmfmm_create(None, ctypes.byref(prm), 0) == lmfmm.ERR_ARG
