@@ -1,0 +1,290 @@
+"""Benchmark of the reaction-field matvec (Mtargets/s) on synthetic inputs.
+
+Default workload: four layers (interfaces z = 0, -1, -2, k = (1, 1.5, 2, 2.5)
++ 0.02i), N = 2^20 points in 64 Gaussian clusters (sigma 0.05) in layers 1-2,
+complex currents, truncation p = 12.  One step = one full matvec
+Phi = A J (P2M, M2M, M2L, L2L, L2P, near field) with the tree and tables
+built beforehand.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--precision fp64|mixed] [--workload four_layer|three_layer|two_layer]
+
+Multi-GPU: every rank runs an independent replica of the workload (the
+reaction components are independent FMMs, no data exchange is needed);
+value = targets processed by all ranks / max-over-ranks time (weak scaling).
+--impl reference times the CPU oracle (direct FP64 Sommerfeld sum) on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# ALU peaks from unit counts and the maximum SM clock (152 SMs, 2070 MHz):
+# FP32 128 FMA/clk/SM, FP64 2 FMA/clk/SM (the nominal 1.25 TFLOP/s).
+SM_COUNT, SM_MHZ = 152, 2070.0
+FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * SM_MHZ * 1e6 / 1e12
+FP64_PEAK_TFLOPS = SM_COUNT * 2 * 2 * SM_MHZ * 1e6 / 1e12
+
+
+def workload(name, seed_shift=0):
+    from paper_2507_18491_gb300 import workloads as W
+    if name == "four_layer":
+        return W.four_layer_clusters(seed=1005 + seed_shift), dict(depth=6, theta=0.55)
+    if name == "three_layer":
+        return W.three_layer(seed=1002 + seed_shift), dict(depth=5, theta=0.55)
+    if name == "three_layer_small":
+        return W.three_layer(n=8192, seed=1002 + seed_shift, p=8), dict(depth=4, theta=0.55)
+    if name == "two_layer":
+        return W.two_layer_small(seed=1001 + seed_shift), dict(depth=2, theta=0.4)
+    raise SystemExit("unknown workload " + name)
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, 0
+    import torch.distributed as dist
+    import torch
+    rank, lrank = int(os.environ["RANK"]), int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(lrank)
+    dist.init_process_group("nccl")
+    return rank, ws, lrank
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(x, ws):
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, idx):
+        self.proc = None
+        self.out = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+        try:
+            os.makedirs(os.path.dirname(self.out), exist_ok=True)
+            self.f = open(self.out, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(idx), "--query-gpu=clocks.sm,clocks.max.sm,power.draw,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.out):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(mx)) if mx else None, "reasons": sorted(reasons)}
+
+
+def cpu_baseline(w, sample_sources=1500, sample_targets=8, threads=0):
+    """The oracle (direct FP64 Sommerfeld sum) on a bounded sample; returns
+    targets/s extrapolated to all N sources."""
+    import oracle
+    rng = np.random.default_rng(0)
+    src = rng.choice(w.N, min(sample_sources, w.N), replace=False)
+    tg = rng.choice(w.N, sample_targets, replace=False)
+    t0 = time.time()
+    oracle.direct(w.d, w.k, w.xyz, w.J, targets=tg, sources=src, nthreads=threads)
+    dt = time.time() - t0
+    pairs_per_s = tg.size * src.size / dt
+    cores = threads or os.cpu_count()
+    return {"value": pairs_per_s / w.N / 1e6, "unit": "Mtargets/s", "cores": cores,
+            "kind": "oracle",
+            "sample": "%d targets x %d of %d sources (direct FP64 Sommerfeld sum), "
+                      "%.1f s wall; targets/s = pairs/s / N" % (tg.size, src.size, w.N, dt)}
+
+
+def accuracy(op, w, nsrc=400, ntg=16):
+    """Err_2 (Section 4) of the matvec against the oracle on a sample: J is
+    kept on nsrc random sources (zero elsewhere), the oracle sums over those
+    sources at ntg random targets."""
+    import torch
+    import oracle
+    rng = np.random.default_rng(11)
+    src = rng.choice(w.N, nsrc, replace=False)
+    tg = rng.choice(w.N, ntg, replace=False)
+    J = np.zeros_like(w.J)
+    J[src] = w.J[src]
+    got = op.matvec(torch.from_numpy(J).to("cuda")).cpu().numpy()
+    ref, _ = oracle.direct(w.d, w.k, w.xyz, J, targets=tg, sources=src)
+    return float(np.linalg.norm(got[tg] - ref) / np.linalg.norm(ref))
+
+
+def run_reference(args):
+    rank, ws, _ = dist_init()
+    if rank != 0:
+        return
+    w, _ = workload(args.workload)
+    per = []
+    for _ in range(args.warmup):
+        cpu_baseline(w, sample_sources=200, sample_targets=2)
+    for _ in range(args.steps):
+        per.append(cpu_baseline(w, sample_sources=600, sample_targets=4))
+    v = float(np.mean([c["value"] for c in per]))
+    cb = dict(per[-1])
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mtargets/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * w.N / (v * 1e6), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "N": w.N, "p": w.p, "layers": int(w.d.size + 1)},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "Mtargets/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+METRIC = "layered Maxwell FMM matvec Mtargets/s at N=1M vs FP64 form at rel err <=1e-6"
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours")
+    ap.add_argument("--precision", default="fp64")
+    ap.add_argument("--workload", default="four_layer")
+    ap.add_argument("--p", type=int, default=0)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    from paper_2507_18491_gb300 import build as B
+    from paper_2507_18491_gb300 import lmfmm
+    rank, ws, lrank = dist_init()
+    dev = lrank if ws > 1 else 0
+    torch.cuda.set_device(dev)
+    B.build()
+    w, opt = workload(args.workload, seed_shift=rank)
+    p = args.p or w.p
+    prec = lmfmm.FP64 if args.precision == "fp64" else lmfmm.MIXED
+    t0 = time.time()
+    op = lmfmm.Operator(w.d, w.k, w.xyz, p=p, depth=opt["depth"], theta=opt["theta"],
+                        precision=prec, device=dev).build()
+    setup_s = time.time() - t0
+    stream = torch.cuda.current_stream()
+    J = torch.from_numpy(w.J).to("cuda")
+    out = torch.empty_like(J)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        op.matvec(J, out)
+    torch.cuda.synchronize()
+    clocks = Clocks(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    m2l_ms = []
+    barrier(ws)
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.fill_(i & 0xff)        # L2 flush between timed steps (outside the events)
+        ev[i][0].record(stream)
+        op.matvec(J, out)
+        ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        m2l_ms.append(op.stats()["ms_stage"]["m2l"])
+    torch.cuda.synchronize()
+    barrier(ws)
+    ck = clocks.stop()
+    total_ms = sum(a.elapsed_time(b) for a, b in ev)
+    total_ms = allmax(total_ms, ws)
+    ms = total_ms / args.steps
+    value = ws * w.N / (ms * 1e-3) / 1e6
+    st = op.stats()
+    # end to end through the host-buffer entry point (pinned host memory)
+    Jh = torch.from_numpy(w.J).pin_memory().numpy()
+    Ph = torch.empty((w.N, 3), dtype=torch.complex128).pin_memory().numpy()
+    lmfmm.matvec_host(op.ctx, Jh, Ph)
+    barrier(ws)
+    t1 = time.time()
+    for _ in range(args.steps):
+        lmfmm.matvec_host(op.ctx, Jh, Ph)
+    e2e_ms = allmax((time.time() - t1) * 1e3 / args.steps, ws)
+    P = (p + 1) ** 2
+    flops = 8.0 * P * P * st["m2l_columns"]
+    m2l_s = float(np.mean(m2l_ms)) * 1e-3
+    achieved = flops / m2l_s / 1e12
+    launches_per_step = 6 + 2 * st["depth"]
+    if prec == lmfmm.FP64:
+        peak, peak_src = FP64_PEAK_TFLOPS, "derived FP64 ALU: 152 SM x 2 FMA/clk x 2 x 2070 MHz"
+    else:
+        peak, peak_src = FP32_PEAK_TFLOPS, "derived FP32 ALU: 152 SM x 128 FMA/clk x 2 x 2070 MHz"
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mtargets/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == lmfmm.FP64 else "f32", "data": "synthetic",
+        "config": {"workload": w.name, "N": w.N, "layers": int(w.d.size + 1), "p": p,
+                   "depth": st["depth"], "theta": opt["theta"], "precision": args.precision,
+                   "components": st["n_components"], "m2l_pairs": st["n_m2l_pairs"],
+                   "geometries": st["n_geometries"], "near_point_pairs": st["n_near_point_pairs"],
+                   "setup_s": round(setup_s, 3), "l2": "flushed (256 MiB write) between steps",
+                   "stage_ms": {k: round(v, 3) for k, v in st["ms_stage"].items()},
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "clocks": ck,
+        "e2e": {"value": ws * w.N / (e2e_ms * 1e-3) / 1e6, "unit": "Mtargets/s",
+                "h2d_bytes_per_step": int(w.N * 3 * 16), "d2h_bytes_per_step": int(w.N * 3 * 16)},
+        "gpu_launches": launches_per_step * args.steps,
+        "roofline": {"kernel": "k_m2l", "bound": "alu", "achieved": achieved,
+                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "peak_source": peak_src, "flops_per_launch": flops},
+    }
+    if rank == 0 and not args.no_cpu:
+        line["config"]["rel_err_vs_oracle"] = accuracy(op, w)
+        line["cpu_baseline"] = cpu_baseline(w)
+    op.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -24,14 +24,15 @@ struct DevState {
     int64_t *leaves = nullptr;
     int64_t nleaves = 0;
     cd *qh = nullptr, *ph = nullptr; // helical, sorted [N][3]
-    cd *me = nullptr, *le = nullptr; // [nbox][3][P]
+    void *me = nullptr, *le = nullptr; // [nbox][3][P], complex T (scaled)
     CompDev *comps = nullptr;
     GeomDev *geoms = nullptr;
-    cd *tab = nullptr;
+    void *tab = nullptr;             // [ngeom][5][P][P], complex T (scaled)
+    LayerScale lscale{};
     M2LPair *m2l = nullptr;
     M2LWork *m2lwork = nullptr;
     int64_t n_m2lwork = 0;
-    cd *tup = nullptr, *tdn = nullptr;
+    void *tup = nullptr, *tdn = nullptr;   // [ngroup][P][P], complex T (scaled)
     int64_t *tchild = nullptr, *tparent = nullptr;
     GemmWork *gwork = nullptr;
     std::vector<int64_t> gwork_off;  // per child level: [off[l], off[l+1])
@@ -41,6 +42,7 @@ struct DevState {
     cd *stage = nullptr;             // [2][N][3] for host-buffer matvec
     cudaEvent_t ev[9]{};
     bool ev_ok = false;
+    bool mv_recorded = false;        // stage events hold a matvec
     double bytes = 0;
 };
 
@@ -84,6 +86,16 @@ lmfmm_status dalloc(lmfmm_ctx *ctx, T **p, size_t count)
     DS(ctx)->bytes += (double)(count * sizeof(T));
     *p = (T *)q;
     return LMFMM_OK;
+}
+
+void dfree(lmfmm_ctx *ctx, void *p)
+{
+    auto &v = DS(ctx)->allocs;
+    auto it = std::find(v.begin(), v.end(), p);
+    if (it != v.end()) {
+        cudaFree(p);
+        v.erase(it);
+    }
 }
 
 template <typename T>
@@ -225,9 +237,9 @@ lmfmm_status lmfmm_create(lmfmm_ctx **out, const lmfmm_params *prm, int device)
                 "depth <= 20)";
         return LMFMM_ERR_ARG;
     }
-    if (prm->precision != LMFMM_FP64) {
-        g_err = "lmfmm_create: only LMFMM_FP64 is implemented in this build";
-        return LMFMM_ERR_UNSUPPORTED;
+    if (prm->precision != LMFMM_FP64 && prm->precision != LMFMM_MIXED) {
+        g_err = "lmfmm_create: precision must be LMFMM_FP64 or LMFMM_MIXED";
+        return LMFMM_ERR_ARG;
     }
     cudaError_t e = cudaSetDevice(device);
     if (e != cudaSuccess) {
@@ -342,8 +354,19 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
     d->nleaves = (int64_t)leaves.size();
     TRY(dalloc(ctx, &d->qh, 3 * N));
     TRY(dalloc(ctx, &d->ph, 3 * N));
-    TRY(dalloc(ctx, &d->me, (size_t)nbox * 3 * P));
-    TRY(dalloc(ctx, &d->le, (size_t)nbox * 3 * P));
+    const bool f32 = ctx->prm.precision == LMFMM_MIXED;
+    const size_t esz = f32 ? sizeof(cf) : sizeof(cd);
+    {
+        unsigned char *q1 = nullptr, *q2 = nullptr;
+        TRY(dalloc(ctx, &q1, (size_t)nbox * 3 * P * esz));
+        TRY(dalloc(ctx, &q2, (size_t)nbox * 3 * P * esz));
+        d->me = q1;
+        d->le = q2;
+    }
+    const double Sroot = 2.0 * ctx->root_h;
+    auto lev_size = [&](int lev) { return Sroot / (double)(1u << lev); };
+    auto kabs = [&](int layer) { return std::hypot(ctx->med.k[layer].x, ctx->med.k[layer].y); };
+    for (int j = 0; j <= ctx->med.L; ++j) d->lscale.s[j] = kabs(j) * lev_size(ctx->depth);
     TRY(dupload(ctx, &d->comps, ctx->comps));
     cd *dG = nullptr;
     int *dcg = nullptr;
@@ -364,6 +387,8 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
         gd.zs = g.zs;
         gd.zt = g.zt;
         gd.plan = geom_plan(a, p, g.rho, c.s * (g.zs - g.zt));
+        gd.scale_s = kabs(c.l) * lev_size(g.level);
+        gd.scale_t = kabs(c.lp) * lev_size(g.level);
         if (plan_nodes(gd.plan) > (1 << 20)) {
             ctx->err = "build: an M2L geometry needs more than 2^20 quadrature nodes";
             return LMFMM_ERR_QUAD;
@@ -372,16 +397,34 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
         gd.tab_index = (int64_t)i;
         hg[i] = gd;
     }
-    TRY(dalloc(ctx, &d->tab, ctx->geoms.size() * (size_t)NTAB * P * P));
-    TRY(tabulate(ctx, hg, d->comps, dG, dcg, d->tab, st));
-    TRY(dupload(ctx, &d->geoms, hg));
+    {
+        // FP64 Chebyshev tabulation, then level scaling (and cast for the mixed form)
+        cd *tab64 = nullptr;
+        TRY(dalloc(ctx, &tab64, ctx->geoms.size() * (size_t)NTAB * P * P));
+        TRY(tabulate(ctx, hg, d->comps, dG, dcg, tab64, st));
+        TRY(dupload(ctx, &d->geoms, hg));
+        if (f32) {
+            cf *t32 = nullptr;
+            TRY(dalloc(ctx, &t32, ctx->geoms.size() * (size_t)NTAB * P * P));
+            launch_scale_tables<float>(p, 0, (int64_t)hg.size(), d->geoms, tab64, t32, st);
+            CK(cudaGetLastError());
+            CK(cudaStreamSynchronize(st));
+            dfree(ctx, tab64);
+            d->tab = t32;
+        } else {
+            launch_scale_tables<double>(p, 0, (int64_t)hg.size(), d->geoms, tab64, tab64, st);
+            CK(cudaGetLastError());
+            d->tab = tab64;
+        }
+    }
     TRY(dupload(ctx, &d->m2l, ctx->m2l));
     std::vector<M2LWork> mw;
     int64_t ncols = 0;
     for (size_t gi = 0; gi < ctx->geoms.size(); ++gi) {
         const Geom &g = ctx->geoms[gi];
         for (int t = 0; t < NTAB; ++t) {
-            int per = (t == 1) ? 32 : 16;
+            int bn = f32 ? gemm_cols<float>() : gemm_cols<double>();
+            int per = (t == 1) ? bn : bn / 2;
             for (int64_t q = g.pair0; q < g.pair1; q += per) {
                 M2LWork w{};
                 w.geom = (int)gi;
@@ -403,13 +446,42 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
         gaunt_table(p, goff, gl, gv);
         size_t ngr = ctx->tgroups.size();
         std::vector<cd> hup(ngr * (size_t)P * P), hdn(ngr * (size_t)P * P);
+        std::vector<int> deg(P);
+        for (int n = 0; n <= p; ++n)
+            for (int m = -n; m <= n; ++m) deg[n * n + n + m] = n;
         for (size_t i = 0; i < ngr; ++i) {
             const TransGroup &g = ctx->tgroups[i];
+            cd *U = &hup[i * P * P], *V = &hdn[i * P * P];
             translation_matrix(p, zc(ctx->med.k[g.layer].x, ctx->med.k[g.layer].y), g.t, goff, gl,
-                               gv, &hup[i * P * P], &hdn[i * P * P]);
+                               gv, U, V);
+            // scaled expansions: M~ = M / s^n, L~ = L s^nu, s = |k| S_level
+            double sc = kabs(g.layer) * lev_size(g.level), sp = kabs(g.layer) * lev_size(g.level - 1);
+            for (int r = 0; r < P; ++r)
+                for (int c = 0; c < P; ++c) {
+                    double fu = std::pow(sc, deg[c]) / std::pow(sp, deg[r]);
+                    double fd = std::pow(sc, deg[r]) / std::pow(sp, deg[c]);
+                    U[r * P + c] = fu * U[r * P + c];
+                    V[r * P + c] = fd * V[r * P + c];
+                }
         }
-        TRY(dupload(ctx, &d->tup, hup));
-        TRY(dupload(ctx, &d->tdn, hdn));
+        if (f32) {
+            std::vector<cf> u32(hup.size()), d32(hdn.size());
+            for (size_t i = 0; i < hup.size(); ++i) {
+                u32[i] = cf{(float)hup[i].x, (float)hup[i].y};
+                d32[i] = cf{(float)hdn[i].x, (float)hdn[i].y};
+            }
+            cf *a1 = nullptr, *a2 = nullptr;
+            TRY(dupload(ctx, &a1, u32));
+            TRY(dupload(ctx, &a2, d32));
+            d->tup = a1;
+            d->tdn = a2;
+        } else {
+            cd *a1 = nullptr, *a2 = nullptr;
+            TRY(dupload(ctx, &a1, hup));
+            TRY(dupload(ctx, &a2, hdn));
+            d->tup = a1;
+            d->tdn = a2;
+        }
         TRY(dupload(ctx, &d->tchild, ctx->tpair_child));
         TRY(dupload(ctx, &d->tparent, ctx->tpair_parent));
         // work items per child level
@@ -420,8 +492,9 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
             for (size_t gi = 0; gi < ctx->tgroups.size(); ++gi) {
                 const TransGroup &g = ctx->tgroups[gi];
                 if (g.level != lev) continue;
-                for (int64_t q = g.pair0; q < g.pair1; q += 10)
-                    gw.push_back(GemmWork{(int)gi, (int)std::min<int64_t>(10, g.pair1 - q), q});
+                int per = (f32 ? gemm_cols<float>() : gemm_cols<double>()) / 3;
+                for (int64_t q = g.pair0; q < g.pair1; q += per)
+                    gw.push_back(GemmWork{(int)gi, (int)std::min<int64_t>(per, g.pair1 - q), q});
             }
         }
         d->gwork_off[ctx->depth + 1] = (int64_t)gw.size();
@@ -455,33 +528,38 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
     return LMFMM_OK;
 }
 
-static lmfmm_status matvec_impl(lmfmm_ctx *ctx, const lmfmm_c128 *J, lmfmm_c128 *Phi,
-                                cudaStream_t st, bool cj)
+extern "C++" {
+template <typename T>
+static lmfmm_status matvec_t(lmfmm_ctx *ctx, const lmfmm_c128 *J, lmfmm_c128 *Phi,
+                             cudaStream_t st, bool cj)
 {
     DevState *d = DS(ctx);
     const int p = ctx->prm.p, P = (p + 1) * (p + 1);
     const int64_t N = ctx->N, nbox = (int64_t)ctx->boxes.size();
+    cx<T> *me = (cx<T> *)d->me, *le = (cx<T> *)d->le;
+    const cx<T> *tup = (const cx<T> *)d->tup, *tdn = (const cx<T> *)d->tdn;
     CK(cudaEventRecord(d->ev[0], st));
     launch_gather_in(N, d->perm, (const cd *)J, d->qh, cj, st);
-    CK(cudaMemsetAsync(d->me, 0, (size_t)nbox * 3 * P * sizeof(cd), st));
-    launch_p2m(p, d->nleaves, d->leaves, d->boxes, d->xyz, d->qh, ctx->med, d->me, st);
+    CK(cudaMemsetAsync(me, 0, (size_t)nbox * 3 * P * sizeof(cx<T>), st));
+    launch_p2m<T>(p, d->nleaves, d->leaves, d->boxes, d->xyz, d->qh, ctx->med, d->lscale, me, st);
     CK(cudaEventRecord(d->ev[1], st));
     for (int lev = ctx->depth; lev >= 1; --lev) {
         int64_t w0 = d->gwork_off[lev], w1 = d->gwork_off[lev + 1];
-        launch_group_gemm(p, w1 - w0, d->gwork + w0, d->tup, d->tchild, d->tparent, d->me,
-                          d->me, true, st);
+        launch_group_gemm_t<T>(p, w1 - w0, d->gwork + w0, tup, d->tchild, d->tparent, me, me, true,
+                               st);
     }
     CK(cudaEventRecord(d->ev[2], st));
-    CK(cudaMemsetAsync(d->le, 0, (size_t)nbox * 3 * P * sizeof(cd), st));
-    launch_m2l(p, d->n_m2lwork, d->m2lwork, d->geoms, d->comps, d->m2l, d->tab, d->me, d->le, st);
+    CK(cudaMemsetAsync(le, 0, (size_t)nbox * 3 * P * sizeof(cx<T>), st));
+    launch_m2l_t<T>(p, d->n_m2lwork, d->m2lwork, d->geoms, d->comps, d->m2l, (const cx<T> *)d->tab,
+                    me, le, st);
     CK(cudaEventRecord(d->ev[3], st));
     for (int lev = 1; lev <= ctx->depth; ++lev) {
         int64_t w0 = d->gwork_off[lev], w1 = d->gwork_off[lev + 1];
-        launch_group_gemm(p, w1 - w0, d->gwork + w0, d->tdn, d->tparent, d->tchild, d->le,
-                          d->le, false, st);
+        launch_group_gemm_t<T>(p, w1 - w0, d->gwork + w0, tdn, d->tparent, d->tchild, le, le, false,
+                               st);
     }
     CK(cudaEventRecord(d->ev[4], st));
-    launch_l2p(p, d->nleaves, d->leaves, d->boxes, d->xyz, d->le, ctx->med, d->ph, st);
+    launch_l2p<T>(p, d->nleaves, d->leaves, d->boxes, d->xyz, le, ctx->med, d->lscale, d->ph, st);
     CK(cudaEventRecord(d->ev[5], st));
     launch_s2t_apply((int64_t)ctx->near.size(), d->near, d->boxes, d->xyz, d->s2t, d->qh, d->ph,
                      st);
@@ -489,8 +567,17 @@ static lmfmm_status matvec_impl(lmfmm_ctx *ctx, const lmfmm_c128 *J, lmfmm_c128 
     launch_scatter_out(N, d->perm, d->ph, (cd *)Phi, cj, st);
     CK(cudaEventRecord(d->ev[7], st));
     CK(cudaGetLastError());
+    d->mv_recorded = true;
     return LMFMM_OK;
 }
+
+static lmfmm_status matvec_impl(lmfmm_ctx *ctx, const lmfmm_c128 *J, lmfmm_c128 *Phi,
+                                cudaStream_t st, bool cj)
+{
+    if (ctx->prm.precision == LMFMM_MIXED) return matvec_t<float>(ctx, J, Phi, st, cj);
+    return matvec_t<double>(ctx, J, Phi, st, cj);
+}
+}  // extern "C++"
 
 lmfmm_status lmfmm_matvec(lmfmm_ctx *ctx, const lmfmm_c128 *J, lmfmm_c128 *Phi, void *stream)
 {
@@ -746,7 +833,7 @@ lmfmm_status lmfmm_get_stats(const lmfmm_ctx *ctx, lmfmm_stats *out)
     lmfmm_ctx *c = (lmfmm_ctx *)ctx;
     *out = c->stats;
     DevState *d = DS(c);
-    if (c->built && d && d->ev_ok && cudaEventQuery(d->ev[7]) == cudaSuccess) {
+    if (c->built && d && d->ev_ok && d->mv_recorded && cudaEventQuery(d->ev[7]) == cudaSuccess) {
         float ms;
         for (int i = 0; i < 6; ++i)
             if (cudaEventElapsedTime(&ms, d->ev[i], d->ev[i + 1]) == cudaSuccess) out->ms_stage[i] = ms;

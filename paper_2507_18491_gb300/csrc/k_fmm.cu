@@ -6,13 +6,6 @@
 
 namespace lmf {
 
-static __device__ inline void decode_nm(int idx, int &n, int &m)
-{
-    n = (int)sqrt((double)idx + 0.5);
-    while ((n + 1) * (n + 1) <= idx) ++n;
-    while (n * n > idx) --n;
-    m = idx - n * n - n;
-}
 
 // ------------------------------------------------------------ permutation
 // q_h[i] = (J_x + i J_y, J_x - i J_y, J_z) of point perm[i] (optionally of conj J)
@@ -55,67 +48,107 @@ void launch_scatter_out(int64_t N, const int64_t *perm, const cd *phih, cd *Phi,
 }
 
 // --------------------------------------------------------------- P2M, L2P
-// basis b_nm(r) = j_n(k |r|) Y_n^m(r^) with Y_n^m = P^_n^|m| e^{i m phi}
-// (times (-1)^m for m < 0); P2M uses 4 pi conj(Y) (eq. mecoeff).
+// basis b_nm(r) = j_n(k |r|) Y_n^m(r^) / s^n with Y_n^m = P^_n^|m| e^{i m phi}
+// (times (-1)^m for m < 0) and the leaf scale s = |k| S_leaf; P2M uses
+// 4 pi conj(Y) (eq. mecoeff).  Computed in double, stored as T.
+// j_n(z) / w^n, n = 0..p, for |z| < 1.5 by the power series
+//   j_n(z) = z^n / (2n+1)!! sum_k (-z^2/2)^k / (k! (2n+3)(2n+5)...(2n+2k+1)),
+// carried out in T with zeta = z/w so that no power of z over- or underflows.
+template <typename T>
+static __device__ inline void sph_bessel_scaled_series(cx<T> z, cx<T> zeta, int p, cx<T> *j)
+{
+    cx<T> q = T(-0.5) * (z * z);
+    cx<T> zn{T(1), T(0)};
+    T df = T(1);   // (2n+1)!!
+    for (int n = 0; n <= p; ++n) {
+        if (n > 0) {
+            zn = zn * zeta;
+            df *= T(2 * n + 1);
+        }
+        cx<T> term{T(1), T(0)}, sum{T(1), T(0)};
+        for (int k = 1; k <= 14; ++k) {
+            term = term * q * (T(1) / (T(k) * T(2 * n + 2 * k + 1)));
+            sum += term;
+            if (abs2(term) < T(1e-18) * abs2(sum)) break;
+        }
+        j[n] = (zn * sum) * (T(1) / df);
+    }
+}
+
+// basis b_nm(r) = scale * j_n(k |r|) Y_n^m(r^) / s^n with Y_n^m = P^_n^|m| e^{i m phi}
+// (times (-1)^m for m < 0), s = |k| S_leaf; P2M uses scale = 4 pi and conj(Y)
+// (eq. mecoeff).  FP64 form in double; mixed form in float when |k r| < 1.5.
+template <typename T>
 static __device__ inline void point_basis(int p, cd k, double dx, double dy, double dz,
-                                          bool conjugate, double scale, cd *out /*[P]*/)
+                                          bool conjugate, double scale, double inv_s, cx<T> *out)
 {
     double r = sqrt(dx * dx + dy * dy + dz * dz);
     double rxy = sqrt(dx * dx + dy * dy);
     double ct = r > 0 ? dz / r : 1.0, st = r > 0 ? rxy / r : 0.0;
-    cd e1 = rxy > 0 ? cd{dx / rxy, dy / rxy} : cd{1.0, 0.0};
+    cx<T> jn[LMF_PMAX + 1];
+    cd kr = k * r;
+    if (sizeof(T) == 4 && cabsd(kr) < 1.5) {
+        cd zeta = (r * inv_s) * k;
+        sph_bessel_scaled_series<T>(cx<T>{(T)kr.x, (T)kr.y}, cx<T>{(T)zeta.x, (T)zeta.y}, p, jn);
+        for (int n = 0; n <= p; ++n) jn[n] = (T)scale * jn[n];
+    } else {
+        cd jd[LMF_PMAX + 1];
+        sph_bessel_seq(kr, p, jd);
+        double sp = scale;
+        for (int n = 0; n <= p; ++n) {
+            jn[n] = cx<T>{(T)(sp * jd[n].x), (T)(sp * jd[n].y)};
+            sp *= inv_s;
+        }
+    }
+    T Pl[(LMF_PMAX + 1) * (LMF_PMAX + 2) / 2];
+    legendre_norm<T>(p, (T)ct, (T)st, Pl);
+    cx<T> e1 = rxy > 0 ? cx<T>{(T)(dx / rxy), (T)(dy / rxy)} : cx<T>{T(1), T(0)};
     if (conjugate) e1 = conj(e1);
-    cd jn[LMF_PMAX + 1];
-    sph_bessel_seq(k * r, p, jn);
-    double Pl[(LMF_PMAX + 1) * (LMF_PMAX + 2) / 2];
-    legendre_norm<double>(p, ct, st, Pl);
-    cd em = mkd(1.0);   // e^{i m phi} (conjugated if requested)
+    cx<T> em{T(1), T(0)};
     for (int m = 0; m <= p; ++m) {
-        cd emc = conj(em);  // e^{-i m phi} ~ the m < 0 phase
+        cx<T> emc = conj(em);
+        T sg = (m & 1) ? T(-1) : T(1);
         for (int n = m; n <= p; ++n) {
-            double v = scale * Pl[(n * (n + 1)) / 2 + m];
-            cd jv = v * jn[n];
+            cx<T> jv = Pl[(n * (n + 1)) / 2 + m] * jn[n];
             out[n * n + n + m] = jv * em;
-            if (m > 0) out[n * n + n - m] = ((m & 1) ? -1.0 : 1.0) * (jv * emc);
+            if (m > 0) out[n * n + n - m] = sg * (jv * emc);
         }
         em = em * e1;
     }
 }
 
+template <typename T>
 __global__ void k_p2m(int p, const int64_t *leaves, const BoxDev *boxes, const double *xyz,
-                      const cd *qh, MediumDev M, cd *me)
+                      const cd *qh, MediumDev M, LayerScale ls, cx<T> *me)
 {
     extern __shared__ unsigned char smraw[];
     const int P = (p + 1) * (p + 1);
     const int CH = 32;
-    cd *bas = (cd *)smraw;          // [CH][P]
-    cd *hq = bas + CH * P;          // [CH][3]
+    cx<T> *bas = (cx<T> *)smraw;    // [CH][P]
+    cx<T> *hq = bas + CH * P;       // [CH][3]
     int64_t bi = leaves[blockIdx.x];
     BoxDev b = boxes[bi];
     cd k = M.k[b.layer];
+    const double inv_s = 1.0 / ls.s[b.layer];
     const int NO = 3 * P;
-    const int PER = (NO + blockDim.x - 1) / blockDim.x;   // <= 8 for P <= 441 w/ 192 thr
-    cd acc[8];
-    for (int i = 0; i < 8; ++i) acc[i] = mkd(0.0);
+    const int PER = (NO + blockDim.x - 1) / blockDim.x;
+    cx<T> acc[8];
+    for (int i = 0; i < 8; ++i) acc[i] = cx<T>{T(0), T(0)};
     for (int64_t c0 = b.p0; c0 < b.p1; c0 += CH) {
         int np = (int)min((int64_t)CH, b.p1 - c0);
-        if (threadIdx.x < CH) {
+        if (threadIdx.x < np) {
             int j = threadIdx.x;
-            if (j < np) {
-                int64_t t = c0 + j;
-                point_basis(p, k, xyz[3 * t] - b.c[0], xyz[3 * t + 1] - b.c[1],
-                            xyz[3 * t + 2] - b.c[2], true, 4.0 * LMF_PI, bas + j * P);
-                hq[3 * j] = qh[3 * t];
-                hq[3 * j + 1] = qh[3 * t + 1];
-                hq[3 * j + 2] = qh[3 * t + 2];
-            }
+            int64_t t = c0 + j;
+            point_basis<T>(p, k, xyz[3 * t] - b.c[0], xyz[3 * t + 1] - b.c[1],
+                           xyz[3 * t + 2] - b.c[2], true, 4.0 * LMF_PI, inv_s, bas + j * P);
+            for (int v = 0; v < 3; ++v) hq[3 * j + v] = cx<T>{(T)qh[3 * t + v].x, (T)qh[3 * t + v].y};
         }
         __syncthreads();
         for (int i = 0; i < PER; ++i) {
             int o = threadIdx.x + i * blockDim.x;
             if (o >= NO) break;
             int v = o / P, nm = o % P;
-            cd a = acc[i];
+            cx<T> a = acc[i];
             for (int j = 0; j < np; ++j) a += hq[3 * j + v] * bas[j * P + nm];
             acc[i] = a;
         }
@@ -127,240 +160,73 @@ __global__ void k_p2m(int p, const int64_t *leaves, const BoxDev *boxes, const d
     }
 }
 
+template <typename T>
 __global__ void k_l2p(int p, const int64_t *leaves, const BoxDev *boxes, const double *xyz,
-                      const cd *le, MediumDev M, cd *ph)
+                      const cx<T> *le, MediumDev M, LayerScale ls, cd *ph)
 {
     extern __shared__ unsigned char smraw[];
     const int P = (p + 1) * (p + 1);
-    cd *L = (cd *)smraw;   // [3][P]
+    cx<T> *L = (cx<T> *)smraw;          // [3][P]
+    cx<T> *bas = L + 3 * P;             // [blockDim][P]
     int64_t bi = leaves[blockIdx.x];
     BoxDev b = boxes[bi];
     for (int e = threadIdx.x; e < 3 * P; e += blockDim.x) L[e] = le[bi * 3 * P + e];
     __syncthreads();
     cd k = M.k[b.layer];
+    const double inv_s = 1.0 / ls.s[b.layer];
+    cx<T> *mb = bas + (size_t)threadIdx.x * P;
     for (int64_t t = b.p0 + threadIdx.x; t < b.p1; t += blockDim.x) {
-        double dx = xyz[3 * t] - b.c[0], dy = xyz[3 * t + 1] - b.c[1], dz = xyz[3 * t + 2] - b.c[2];
-        double r = sqrt(dx * dx + dy * dy + dz * dz);
-        double rxy = sqrt(dx * dx + dy * dy);
-        double ct = r > 0 ? dz / r : 1.0, st = r > 0 ? rxy / r : 0.0;
-        cd e1 = rxy > 0 ? cd{dx / rxy, dy / rxy} : cd{1.0, 0.0};
-        cd jn[LMF_PMAX + 1];
-        sph_bessel_seq(k * r, p, jn);
-        double Pl[(LMF_PMAX + 1) * (LMF_PMAX + 2) / 2];
-        legendre_norm<double>(p, ct, st, Pl);
-        cd A = mkd(0.0), B = mkd(0.0), C = mkd(0.0);
-        cd em = mkd(1.0);
-        for (int m = 0; m <= p; ++m) {
-            cd emc = conj(em);
-            double sg = (m & 1) ? -1.0 : 1.0;
-            for (int n = m; n <= p; ++n) {
-                cd jv = Pl[(n * (n + 1)) / 2 + m] * jn[n];
-                cd bp = jv * em;
-                int ip = n * n + n + m;
-                A += L[ip] * bp;
-                B += L[P + ip] * bp;
-                C += L[2 * P + ip] * bp;
-                if (m > 0) {
-                    cd bm = sg * (jv * emc);
-                    int im = n * n + n - m;
-                    A += L[im] * bm;
-                    B += L[P + im] * bm;
-                    C += L[2 * P + im] * bm;
-                }
-            }
-            em = em * e1;
+        point_basis<T>(p, k, xyz[3 * t] - b.c[0], xyz[3 * t + 1] - b.c[1], xyz[3 * t + 2] - b.c[2],
+                       false, 1.0, inv_s, mb);
+        cx<T> A{T(0), T(0)}, B{T(0), T(0)}, C{T(0), T(0)};
+        for (int i = 0; i < P; ++i) {
+            cx<T> bv = mb[i];
+            A += L[i] * bv;
+            B += L[P + i] * bv;
+            C += L[2 * P + i] * bv;
         }
-        ph[3 * t] = A;
-        ph[3 * t + 1] = B;
-        ph[3 * t + 2] = C;
+        ph[3 * t] = cd{(double)A.x, (double)A.y};
+        ph[3 * t + 1] = cd{(double)B.x, (double)B.y};
+        ph[3 * t + 2] = cd{(double)C.x, (double)C.y};
     }
 }
 
+template <typename T>
 void launch_p2m(int p, int64_t nleaf, const int64_t *leaves, const BoxDev *boxes,
-                const double *xyz, const cd *qh, const MediumDev &M, cd *me, cudaStream_t st)
+                const double *xyz, const cd *qh, const MediumDev &M, const LayerScale &ls,
+                cx<T> *me, cudaStream_t st)
 {
     if (nleaf <= 0) return;
     const int P = (p + 1) * (p + 1);
-    size_t sm = (size_t)(32 * P + 32 * 3) * sizeof(cd);
+    size_t sm = (size_t)(32 * P + 32 * 3) * sizeof(cx<T>);
     int thr = 3 * P <= 8 * 128 ? 128 : 256;
-    k_p2m<<<(unsigned)nleaf, thr, sm, st>>>(p, leaves, boxes, xyz, qh, M, me);
+    k_p2m<T><<<(unsigned)nleaf, thr, sm, st>>>(p, leaves, boxes, xyz, qh, M, ls, me);
 }
 
+template <typename T>
 void launch_l2p(int p, int64_t nleaf, const int64_t *leaves, const BoxDev *boxes,
-                const double *xyz, const cd *le, const MediumDev &M, cd *phih, cudaStream_t st)
+                const double *xyz, const cx<T> *le, const MediumDev &M, const LayerScale &ls,
+                cd *phih, cudaStream_t st)
 {
     if (nleaf <= 0) return;
     const int P = (p + 1) * (p + 1);
-    k_l2p<<<(unsigned)nleaf, 64, 3 * P * sizeof(cd), st>>>(p, leaves, boxes, xyz, le, M, phih);
+    const int thr = 64;
+    size_t sm = (size_t)(3 * P + thr * P) * sizeof(cx<T>);
+    k_l2p<T><<<(unsigned)nleaf, thr, sm, st>>>(p, leaves, boxes, xyz, le, M, ls, phih);
 }
 
-// ---------------------------------------------------------------- GEMM core
-// Y(P x ncol) = A(P x P) X(P x NC smem); store(r, c, y) for c < ncol.
-// 256 threads: column c = tid % NC, row group tid / NC.
-template <int NC, int RCH, typename Store>
-__device__ inline void gemm_core(int P, const cd *__restrict__ A, const cd *X, int ncol,
-                                 Store store)
-{
-    const int c = threadIdx.x % NC, rg = threadIdx.x / NC, nrg = blockDim.x / NC;
-    for (int r0 = rg; r0 < P; r0 += nrg * RCH) {
-        cd acc[RCH];
-        for (int i = 0; i < RCH; ++i) acc[i] = mkd(0.0);
-        for (int k = 0; k < P; ++k) {
-            cd x = X[k * NC + c];
-#pragma unroll
-            for (int i = 0; i < RCH; ++i) {
-                int r = r0 + i * nrg;
-                if (r < P) {
-                    double2 av = __ldg((const double2 *)(A + (int64_t)r * P + k));
-                    acc[i] += cd{av.x, av.y} * x;
-                }
-            }
-        }
-        if (c < ncol)
-            for (int i = 0; i < RCH; ++i) {
-                int r = r0 + i * nrg;
-                if (r < P) store(r, c, acc[i]);
-            }
-    }
-}
-
-// M2M (atomic, child -> parent) and L2L (child += parent), columns = (pair, v)
-__global__ void k_group_gemm(int p, const GemmWork *work, const cd *mats, const int64_t *src,
-                             const int64_t *dst, const cd *in, cd *out, int atomic)
-{
-    extern __shared__ unsigned char smraw[];
-    const int P = (p + 1) * (p + 1);
-    const int NC = 30;   // 10 pairs x 3 helical components (padded to 32 columns)
-    cd *X = (cd *)smraw; // [P][32]
-    GemmWork w = work[blockIdx.x];
-    int ncol = 3 * w.npair;
-    for (int e = threadIdx.x; e < P * 32; e += blockDim.x) {
-        int k = e / 32, col = e % 32;
-        cd v = mkd(0.0);
-        if (col < ncol) {
-            int pp = col / 3, vv = col % 3;
-            v = in[(src[w.pair0 + pp] * 3 + vv) * P + k];
-        }
-        X[e] = v;
-    }
-    __syncthreads();
-    const cd *A = mats + (int64_t)w.group * P * P;
-    auto store = [&](int r, int col, cd y) {
-        int pp = col / 3, vv = col % 3;
-        cd *o = out + (dst[w.pair0 + pp] * 3 + vv) * P + r;
-        if (atomic) {
-            atomicAdd(&o->x, y.x);
-            atomicAdd(&o->y, y.y);
-        } else {
-            *o += y;
-        }
-    };
-    gemm_core<32, 6>(P, A, X, ncol, store);
-    (void)NC;
-}
-
-void launch_group_gemm(int p, int64_t nwork, const GemmWork *work, const cd *mats,
-                       const int64_t *src, const int64_t *dst, const cd *in, cd *out,
-                       bool atomic, cudaStream_t st)
-{
-    if (nwork <= 0) return;
-    const int P = (p + 1) * (p + 1);
-    size_t sm = (size_t)P * 32 * sizeof(cd);
-    k_group_gemm<<<(unsigned)nwork, 256, sm, st>>>(p, work, mats, src, dst, in, out, atomic);
-}
-
-// --------------------------------------------------------------------- M2L
-// Column roles per table t: (input helical v, signed kappa, coefficient,
-// output helical v) for
-//   A' = 1/2 T0[s1] a - 1/2 T2[s3] b + T1[s2] c
-//   B' = 1/2 T0[s1] b - 1/2 T-2[s3] a + T-1[s2] c
-//   C' = T0[s5] c + 1/2 T-1[s4] a + 1/2 T1[s4] b
-struct ColSpec { int vin, kap; double coef; int vout; };
-__constant__ ColSpec c_cols[5][2] = {
-    {{0, 0, 0.5, 0}, {1, 0, 0.5, 1}},     // (s1, 0)
-    {{2, 0, 1.0, 2}, {2, 0, 1.0, 2}},     // (s5, 0)  (one column)
-    {{2, 1, 1.0, 0}, {2, -1, 1.0, 1}},    // (s2, 1)
-    {{1, 1, 0.5, 2}, {0, -1, 0.5, 2}},    // (s4, 1)
-    {{1, 2, -0.5, 0}, {0, -2, -0.5, 1}},  // (s3, 2)
-};
-
-// The M2L of eq. M2L_scale_with_Tnmu with T = (-i)^nu i^(n'+1+d) s^(nu+mu+n'+m')
-// e^{i d phi} I-hat, d = m' - mu + kappa, factorised as
-//   in(n',m')  = (i s)^(n'+m') e^{i m' phi}  [x (-1)^(n'+m') for a mirrored source]
-//   out(nu,mu) = (-i s)^(nu+mu) e^{-i mu phi} [x (-1)^(nu+mu) for a mirrored target]
-//   const      = i^(1+kappa) e^{i kappa phi} x coefficient.
-// kappa < 0 uses I-hat_{-kappa}[nu,mu,n',m'] = (-1)^kappa I-hat_kappa[nu,-mu,n',-m']:
-// the input column is flipped in m before the product, the output after.
-__global__ void k_m2l(int p, const M2LWork *work, const GeomDev *geoms, const CompDev *comps,
-                      const M2LPair *pairs, const cd *tab, const cd *me, cd *le)
-{
-    extern __shared__ unsigned char smraw[];
-    const int P = (p + 1) * (p + 1);
-    cd *X = (cd *)smraw;   // [P][32]
-    M2LWork w = work[blockIdx.x];
-    const GeomDev &g = geoms[w.geom];
-    const CompDev c = comps[g.comp];
-    const int t = w.t;
-    const int ncpp = (t == 1) ? 1 : 2;
-    const int ncol = w.npair * ncpp;
-    const double s = c.s;
-    for (int e = threadIdx.x; e < P * 32; e += blockDim.x) {
-        int k = e / 32, col = e % 32;
-        cd v = mkd(0.0);
-        if (col < ncol) {
-            int pp = col / ncpp, j = col % ncpp;
-            ColSpec cs = c_cols[t][j];
-            M2LPair pr = pairs[w.pair0 + pp];
-            int n, m;
-            decode_nm(k, n, m);
-            int ms = cs.kap < 0 ? -m : m;
-            cd x = me[(pr.src * 3 + cs.vin) * P + n * n + n + ms];
-            // in(n, ms)
-            int e1 = n + ms;
-            cd sc = ipow<double>(e1);
-            if (s < 0 && (e1 & 1)) sc = -sc;
-            if (c.has_src_refl && (e1 & 1)) sc = -sc;
-            double phi = atan2(pr.sphi, pr.cphi), sn, cs_;
-            sincos(ms * phi, &sn, &cs_);
-            v = sc * (cd{cs_, sn} * x);
-        }
-        X[e] = v;
-    }
-    __syncthreads();
-    const cd *A = tab + ((int64_t)g.tab_index * NTAB + t) * P * P;
-    auto store = [&](int r, int col, cd y) {
-        int pp = col / ncpp, j = col % ncpp;
-        ColSpec cs = c_cols[t][j];
-        M2LPair pr = pairs[w.pair0 + pp];
-        int nu, mh;
-        decode_nm(r, nu, mh);
-        int mu = cs.kap < 0 ? -mh : mh;
-        int e2 = nu + mu;
-        cd sc = ipow<double>(-e2);   // (-i)^(nu+mu)
-        if (s < 0 && (e2 & 1)) sc = -sc;
-        if (c.has_tgt_refl && (e2 & 1)) sc = -sc;
-        double phi = atan2(pr.sphi, pr.cphi), sn, cs_;
-        sincos((cs.kap - mu) * phi, &sn, &cs_);
-        cd k1 = ipow<double>(1 + cs.kap);
-        double cf = cs.coef;
-        if (cs.kap < 0 && (cs.kap & 1)) cf = -cf;
-        cd yy = cf * (sc * (k1 * (cd{cs_, sn} * y)));
-        cd *o = le + (pr.tgt * 3 + cs.vout) * P + nu * nu + nu + mu;
-        atomicAdd(&o->x, yy.x);
-        atomicAdd(&o->y, yy.y);
-    };
-    gemm_core<32, 6>(P, A, X, ncol, store);
-}
-
-void launch_m2l(int p, int64_t nwork, const M2LWork *work, const GeomDev *geoms,
-                const CompDev *comps, const M2LPair *pairs, const cd *tab, const cd *me, cd *le,
-                cudaStream_t st)
-{
-    if (nwork <= 0) return;
-    const int P = (p + 1) * (p + 1);
-    size_t sm = (size_t)P * 32 * sizeof(cd);
-    k_m2l<<<(unsigned)nwork, 256, sm, st>>>(p, work, geoms, comps, pairs, tab, me, le);
-}
+template void launch_p2m<float>(int, int64_t, const int64_t *, const BoxDev *, const double *,
+                                const cd *, const MediumDev &, const LayerScale &, cf *,
+                                cudaStream_t);
+template void launch_p2m<double>(int, int64_t, const int64_t *, const BoxDev *, const double *,
+                                 const cd *, const MediumDev &, const LayerScale &, cd *,
+                                 cudaStream_t);
+template void launch_l2p<float>(int, int64_t, const int64_t *, const BoxDev *, const double *,
+                                const cf *, const MediumDev &, const LayerScale &, cd *,
+                                cudaStream_t);
+template void launch_l2p<double>(int, int64_t, const int64_t *, const BoxDev *, const double *,
+                                 const cd *, const MediumDev &, const LayerScale &, cd *,
+                                 cudaStream_t);
 
 // --------------------------------------------------------------------- S2T
 // For every point pair (j in the source leaf, i in the target leaf) of a near
@@ -531,9 +397,10 @@ cudaError_t configure_fmm_kernels()
 {
     const int big = 200 * 1024;
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_p2m, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-    if ((e = cudaFuncSetAttribute(k_group_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-    if ((e = cudaFuncSetAttribute(k_m2l, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-    return cudaSuccess;
+    if ((e = cudaFuncSetAttribute(k_p2m<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_p2m<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_l2p<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_l2p<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    return configure_trans_kernels();
 }
 }  // namespace lmf

@@ -25,11 +25,16 @@ struct QuadPlanDev {
 struct GeomDev {
     int comp, src_primary;
     double rho, zs, zt;
+    double scale_s, scale_t;  // |k| S_level of the source and target layers
     QuadPlanDev plan;
     int64_t node0;      // first node within its tabulation batch
     int64_t stride;     // node count of its batch (factor-array stride)
     int64_t tab_index;  // table slot
     int batch, pad;
+};
+
+struct LayerScale {      // |k_l| S_leaf per layer (expansion scaling at the leaves)
+    double s[LMF_MAXL + 1];
 };
 
 struct TransGroupDev {
@@ -67,16 +72,29 @@ void launch_gather_in(int64_t N, const int64_t *perm, const cd *J, cd *qh, bool 
                       cudaStream_t st);
 void launch_scatter_out(int64_t N, const int64_t *perm, const cd *phih, cd *Phi, bool conj_out,
                         cudaStream_t st);
+template <typename T>
 void launch_p2m(int p, int64_t nleaf, const int64_t *leaves, const BoxDev *boxes,
-                const double *xyz, const cd *qh, const MediumDev &M, cd *me, cudaStream_t st);
+                const double *xyz, const cd *qh, const MediumDev &M, const LayerScale &ls,
+                cx<T> *me, cudaStream_t st);
+template <typename T>
 void launch_l2p(int p, int64_t nleaf, const int64_t *leaves, const BoxDev *boxes,
-                const double *xyz, const cd *le, const MediumDev &M, cd *phih, cudaStream_t st);
-void launch_group_gemm(int p, int64_t nwork, const GemmWork *work, const cd *mats,
-                       const int64_t *src, const int64_t *dst, const cd *in, cd *out,
-                       bool atomic, cudaStream_t st);
-void launch_m2l(int p, int64_t nwork, const M2LWork *work, const GeomDev *geoms,
-                const CompDev *comps, const M2LPair *pairs, const cd *tab, const cd *me, cd *le,
-                cudaStream_t st);
+                const double *xyz, const cx<T> *le, const MediumDev &M, const LayerScale &ls,
+                cd *phih, cudaStream_t st);
+
+// k_trans.cu
+cudaError_t configure_trans_kernels();
+template <typename T> int gemm_cols();
+template <typename T>
+void launch_group_gemm_t(int p, int64_t nwork, const GemmWork *work, const cx<T> *mats,
+                         const int64_t *src, const int64_t *dst, const cx<T> *in, cx<T> *out,
+                         bool atomic, cudaStream_t st);
+template <typename T>
+void launch_m2l_t(int p, int64_t nwork, const M2LWork *work, const GeomDev *geoms,
+                  const CompDev *comps, const M2LPair *pairs, const cx<T> *tab, const cx<T> *me,
+                  cx<T> *le, cudaStream_t st);
+template <typename T>
+void launch_scale_tables(int p, int64_t g0, int64_t ng, const GeomDev *geoms, const cd *tab64,
+                         cx<T> *tab, cudaStream_t st);
 void launch_s2t_pre(int64_t nnear, const NearPair *near, const BoxDev *boxes, const double *xyz,
                     const MediumDev &M, const CompDev *comps, double a, double kp, cd *coef,
                     int *dflag, cudaStream_t st);

@@ -194,3 +194,36 @@ def test_errors_are_reported_not_raised_on_device():
             lmfmm.set_layers(ctx, [0.0], [1.0, 2.0 - 0.1j])
     finally:
         lmfmm.destroy(ctx)
+
+
+def test_mixed_form_meets_its_bar():
+    """FP32 translations (scaled expansions) against the oracle at 1e-5, and
+    against the FP64 form of the same operator."""
+    w = W.three_layer(n=8192, p=10, depth=4)
+    rng = np.random.default_rng(4)
+    src = rng.choice(w.N, 400, replace=False)
+    J = np.zeros_like(w.J)
+    J[src] = w.J[src]
+    Jt = torch.from_numpy(J).cuda()
+    op64 = lmfmm.Operator(w.d, w.k, w.xyz, p=10, depth=4, theta=0.5).build()
+    a = op64.matvec(Jt).cpu().numpy()
+    op64.close()
+    op32 = lmfmm.Operator(w.d, w.k, w.xyz, p=10, depth=4, theta=0.5,
+                          precision=lmfmm.MIXED).build()
+    b = op32.matvec(Jt).cpu().numpy()
+    op32.close()
+    tg = rng.choice(w.N, 48, replace=False)
+    ref, _ = O.direct(w.d, w.k, w.xyz, J, targets=tg, sources=src)
+    assert rel(b[tg], ref) < 1e-5
+    assert rel(b, a) < 2e-6
+
+
+def test_stats_before_first_matvec():
+    w = W.two_layer_small(n=200, seed=5)
+    op = lmfmm.Operator(w.d, w.k, w.xyz, p=6, depth=2).build()
+    st = op.stats()
+    assert st["n_points"] == 200 and st["ms_stage"]["total"] == 0
+    op.matvec(torch.from_numpy(w.J).cuda())
+    torch.cuda.synchronize()
+    assert op.stats()["ms_stage"]["total"] > 0
+    op.close()
