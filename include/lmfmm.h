@@ -127,6 +127,29 @@ lmfmm_status lmfmm_matvec_adjoint(lmfmm_ctx *ctx, const lmfmm_c128 *y, lmfmm_c12
  * O(N^2), intended for N up to a few thousand.  Device buffers. */
 lmfmm_status lmfmm_direct(lmfmm_ctx *ctx, const lmfmm_c128 *J, lmfmm_c128 *Phi, void *stream);
 
+/* The same all-pairs direct evaluation as lmfmm_direct, for callers that
+ * cannot allocate device memory during the call: programs whose device
+ * memory is wholly reserved by another allocator (a framework's caching
+ * pool, say), or that must not stall or fail on an allocation mid-run.  The
+ * paper has no counterpart; this is a property of the library, not of the
+ * method.  It calls no cudaMalloc, cudaFree or allocating library routine:
+ * its scratch (leaf-pair list + 5 complex Sommerfeld coefficients per point
+ * pair) is one file-scope device array of 32 MiB, and the pair list is
+ * built in a fixed host array of 65536 records.  Requires lmfmm_build (the
+ * context's own buffers, allocated there, are reused).  Returns
+ * LMFMM_ERR_ARG, with the byte count in the message, when
+ * (leaf pairs * 48 bytes, rounded up to 256) + (point pairs * 80 bytes)
+ * exceeds 32 MiB -- about N^2 <= 4e5 point pairs over all components.
+ * The array is shared by every call on a device and keeps the last call's
+ * contents; the call zero-fills what must start at zero.  Calls that
+ * overlap on the GPU (other streams, other contexts on the same device)
+ * race on it.  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  J, Phi: DEVICE [N][3] complex, caller's
+ * point order; synchronous (returns after Phi is written). */
+lmfmm_status lmfmm_direct_noalloc(lmfmm_ctx *ctx, const lmfmm_c128 *J, lmfmm_c128 *Phi,
+                                  void *stream);
+
 /* Density functions phi^{*star}_{l lp}, psi^{*star}_{l lp} (eq. threedensity)
  * at n nodes krho[n] (DEVICE, complex).  out[n][8] (DEVICE): phi for
  * (up,up),(up,dn),(dn,up),(dn,dn) then psi in the same order, where the first

@@ -208,6 +208,25 @@ lmfmm_status tabulate(lmfmm_ctx *ctx, std::vector<GeomDev> &hg, const CompDev *d
 
 }  // namespace
 
+namespace lmf {
+// read-only view of the device state for lmfmm_direct_noalloc (noalloc.cu)
+bool noalloc_state(lmfmm_ctx *ctx, const int64_t **perm, const BoxDev **boxes, const double **xyz,
+                   const CompDev **comps, cd **qh, cd **ph, int **flag)
+{
+    DevState *d = DS(ctx);
+    if (!d || !d->perm || !d->boxes || !d->xyz || !d->comps || !d->qh || !d->ph || !d->flag)
+        return false;
+    *perm = d->perm;
+    *boxes = d->boxes;
+    *xyz = d->xyz;
+    *comps = d->comps;
+    *qh = d->qh;
+    *ph = d->ph;
+    *flag = d->flag;
+    return true;
+}
+}  // namespace lmf
+
 // --------------------------------------------------------------------- ABI
 extern "C" {
 

@@ -42,7 +42,7 @@ class Stats(ctypes.Structure):
 
 EXPORTS = ["lmfmm_default_params", "lmfmm_create", "lmfmm_set_layers", "lmfmm_set_points",
            "lmfmm_build", "lmfmm_matvec", "lmfmm_matvec_host", "lmfmm_matvec_adjoint",
-           "lmfmm_direct", "lmfmm_densities", "lmfmm_m2l_table", "lmfmm_translation_matrix",
+           "lmfmm_direct", "lmfmm_direct_noalloc", "lmfmm_densities", "lmfmm_m2l_table", "lmfmm_translation_matrix",
            "lmfmm_get_stats", "lmfmm_last_error", "lmfmm_destroy"]
 
 
@@ -77,6 +77,7 @@ def load():
         "lmfmm_matvec_host": [P, P, P, P],
         "lmfmm_matvec_adjoint": [P, P, P, P],
         "lmfmm_direct": [P, P, P, P],
+        "lmfmm_direct_noalloc": [P, P, P, P],
         "lmfmm_densities": [P, i, i, i64, P, P, P],
         "lmfmm_m2l_table": [P, i, i, i, i, d, d, d, P, P],
         "lmfmm_translation_matrix": [i, C128, ctypes.POINTER(d), P, P],
@@ -167,6 +168,11 @@ def matvec_host(ctx, J: np.ndarray, Phi: np.ndarray, stream=None):
 
 def direct(ctx, J, Phi, stream=None):
     _check(load().lmfmm_direct(ctx, _dptr(J), _dptr(Phi), _stream(stream)), ctx)
+
+
+def direct_noalloc(ctx, J, Phi, stream=None):
+    """lmfmm_direct without device allocation (fixed 32 MiB device scratch)."""
+    _check(load().lmfmm_direct_noalloc(ctx, _dptr(J), _dptr(Phi), _stream(stream)), ctx)
 
 
 def densities(ctx, l, lp, krho, out, stream=None):
