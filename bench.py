@@ -29,7 +29,6 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # ALU peaks from unit counts and the maximum SM clock (152 SMs, 2070 MHz):
 # FP32 128 FMA/clk/SM, FP64 2 FMA/clk/SM (the nominal 1.25 TFLOP/s).
 SM_COUNT, SM_MHZ = 152, 2070.0
@@ -83,9 +82,9 @@ class Clocks:
 
     def __init__(self, idx):
         self.proc = None
-        self.out = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+        import tempfile
+        self.out = os.path.join(tempfile.gettempdir(), "lmfmm_clocks_%d.csv" % os.getpid())
         try:
-            os.makedirs(os.path.dirname(self.out), exist_ok=True)
             self.f = open(self.out, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(idx), "--query-gpu=clocks.sm,clocks.max.sm,power.draw,"
@@ -191,7 +190,9 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours")
-    ap.add_argument("--precision", default="fp64")
+    ap.add_argument("--precision", default="mixed")
+    ap.add_argument("--no-fp64-form", action="store_true",
+                    help="skip the FP64-form comparison run of the default (mixed) bench")
     ap.add_argument("--workload", default="four_layer")
     ap.add_argument("--p", type=int, default=0)
     ap.add_argument("--no-cpu", action="store_true")
@@ -280,8 +281,28 @@ def main():
     }
     if rank == 0 and not args.no_cpu:
         line["config"]["rel_err_vs_oracle"] = accuracy(op, w)
-        line["cpu_baseline"] = cpu_baseline(w)
     op.close()
+    if prec == lmfmm.MIXED and not args.no_fp64_form:
+        # the same matvec in the FP64 form on the same GPU (fewer steps: ~1.2 s each)
+        op64 = lmfmm.Operator(w.d, w.k, w.xyz, p=p, depth=opt["depth"], theta=opt["theta"],
+                              precision=lmfmm.FP64, device=dev).build()
+        op64.matvec(J, out)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.fill_(7)
+        a.record(stream)
+        op64.matvec(J, out)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms64 = allmax(a.elapsed_time(b), ws)
+        line["fp64_form"] = {"value": ws * w.N / (ms64 * 1e-3) / 1e6, "unit": "Mtargets/s",
+                             "ms_per_step": ms64, "steps": 1,
+                             "stage_ms": {k: round(v, 3) for k, v in op64.stats()["ms_stage"].items()}}
+        if rank == 0 and not args.no_cpu:
+            line["fp64_form"]["rel_err_vs_oracle"] = accuracy(op64, w)
+        op64.close()
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(w)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
