@@ -64,6 +64,9 @@ typedef struct {
     double eta;        /* ... and its vertical transmission distance is >= eta * |c_s - c_t| */
     double quad_tol;   /* relative cut-off of the k_rho tails (>= 1e-16) */
     int precision;     /* LMFMM_FP64 or LMFMM_MIXED (FP32 translation arithmetic) */
+    int tensor_cores;  /* mixed form only: 1 runs the M2L products on the tcgen05 tensor cores
+                          (FP32 accuracy by a three-term TF32 split; p <= 15), 0 on the
+                          FP32 SIMT pipes.  Ignored by the FP64 form. */
 } lmfmm_params;
 
 typedef struct {
@@ -81,10 +84,12 @@ typedef struct {
     double ms_setup;       /* wall time of the last lmfmm_build */
     double ms_stage[8];    /* last matvec: P2M, M2M, M2L, L2L, L2P, S2T, permute, total */
     int64_t m2l_columns;   /* helical columns pushed through M2L tables per matvec */
+    int m2l_kernel;        /* M2L product of the built form: 0 FP64 SIMT, 1 FP32 SIMT,
+                              2 tcgen05 tensor cores (three-term TF32) */
 } lmfmm_stats;
 
 /* Fill *prm with defaults (p = 8, depth from leaf_cap = 64, theta = 0.55,
- * eta = 0.1, quad_tol = 1e-15, FP64). */
+ * eta = 0.1, quad_tol = 1e-15, FP64, tensor_cores = 1). */
 lmfmm_status lmfmm_default_params(lmfmm_params *prm);
 
 /* Create a context on CUDA device `device`.  *out receives the handle. */

@@ -6,6 +6,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <string>
+#include <type_traits>
 
 #include "kernels.cuh"
 #include "quad.cuh"
@@ -39,6 +41,8 @@ struct DevState {
     NearPair *near = nullptr;
     cd *s2t = nullptr;
     int *flag = nullptr;
+    int *mvstatus = nullptr;         // matvec status word (bit 4: tensor-core wait gave up)
+    bool m2l_tc = false;             // mixed-form M2L on the tcgen05 tensor cores
     cd *stage = nullptr;             // [2][N][3] for host-buffer matvec
     cudaEvent_t ev[9]{};
     bool ev_ok = false;
@@ -131,6 +135,19 @@ lmfmm_status check_flag(lmfmm_ctx *ctx)
     if (f) {
         ctx->err = "device quadrature hit its cap (flag " + std::to_string(f) + ")";
         return LMFMM_ERR_QUAD;
+    }
+    return LMFMM_OK;
+}
+
+// Status word of the matvec kernels (sticky until the next build): a
+// tensor-core wait that gave up leaves bit 4.
+lmfmm_status check_mvstatus(lmfmm_ctx *ctx)
+{
+    int f = 0;
+    CK(cudaMemcpy(&f, DS(ctx)->mvstatus, sizeof(int), cudaMemcpyDeviceToHost));
+    if (f) {
+        ctx->err = "matvec: a tensor-core wait gave up (status " + std::to_string(f) + ")";
+        return LMFMM_ERR_CUDA;
     }
     return LMFMM_OK;
 }
@@ -240,6 +257,7 @@ lmfmm_status lmfmm_default_params(lmfmm_params *prm)
     prm->eta = 0.1;
     prm->quad_tol = 1e-15;
     prm->precision = LMFMM_FP64;
+    prm->tensor_cores = 1;
     return LMFMM_OK;
 }
 
@@ -258,6 +276,10 @@ lmfmm_status lmfmm_create(lmfmm_ctx **out, const lmfmm_params *prm, int device)
     }
     if (prm->precision != LMFMM_FP64 && prm->precision != LMFMM_MIXED) {
         g_err = "lmfmm_create: precision must be LMFMM_FP64 or LMFMM_MIXED";
+        return LMFMM_ERR_ARG;
+    }
+    if (prm->tensor_cores != 0 && prm->tensor_cores != 1) {
+        g_err = "lmfmm_create: tensor_cores must be 0 or 1";
         return LMFMM_ERR_ARG;
     }
     cudaError_t e = cudaSetDevice(device);
@@ -356,6 +378,9 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
     CK(cudaMalloc((void **)&d->flag, sizeof(int)));
     d->allocs.push_back(d->flag);
     CK(cudaMemset(d->flag, 0, sizeof(int)));
+    CK(cudaMalloc((void **)&d->mvstatus, sizeof(int)));
+    d->allocs.push_back(d->mvstatus);
+    CK(cudaMemset(d->mvstatus, 0, sizeof(int)));
     for (auto &e : d->ev) CK(cudaEventCreate(&e));
     d->ev_ok = true;
     // points and boxes
@@ -374,6 +399,7 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
     TRY(dalloc(ctx, &d->qh, 3 * N));
     TRY(dalloc(ctx, &d->ph, 3 * N));
     const bool f32 = ctx->prm.precision == LMFMM_MIXED;
+    d->m2l_tc = f32 && ctx->prm.tensor_cores && m2l_tc_supported(p);
     const size_t esz = f32 ? sizeof(cf) : sizeof(cd);
     {
         unsigned char *q1 = nullptr, *q2 = nullptr;
@@ -442,7 +468,7 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
     for (size_t gi = 0; gi < ctx->geoms.size(); ++gi) {
         const Geom &g = ctx->geoms[gi];
         for (int t = 0; t < NTAB; ++t) {
-            int bn = f32 ? gemm_cols<float>() : gemm_cols<double>();
+            int bn = d->m2l_tc ? m2l_tc_cols() : f32 ? gemm_cols<float>() : gemm_cols<double>();
             int per = (t == 1) ? bn : bn / 2;
             for (int64_t q = g.pair0; q < g.pair1; q += per) {
                 M2LWork w{};
@@ -544,6 +570,7 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
     S.bytes_tables = (double)ctx->geoms.size() * NTAB * P * P * 16.0;
     S.ms_setup = std::chrono::duration<double, std::milli>(t1 - t0).count();
     S.m2l_columns = ncols;
+    S.m2l_kernel = d->m2l_tc ? 2 : f32 ? 1 : 0;
     return LMFMM_OK;
 }
 
@@ -569,8 +596,17 @@ static lmfmm_status matvec_t(lmfmm_ctx *ctx, const lmfmm_c128 *J, lmfmm_c128 *Ph
     }
     CK(cudaEventRecord(d->ev[2], st));
     CK(cudaMemsetAsync(le, 0, (size_t)nbox * 3 * P * sizeof(cx<T>), st));
-    launch_m2l_t<T>(p, d->n_m2lwork, d->m2lwork, d->geoms, d->comps, d->m2l, (const cx<T> *)d->tab,
-                    me, le, st);
+    if constexpr (std::is_same<T, float>::value) {
+        if (d->m2l_tc)
+            CK(launch_m2l_tc(p, d->n_m2lwork, d->m2lwork, d->geoms, d->comps, d->m2l,
+                             (const cf *)d->tab, me, le, d->mvstatus, st));
+        else
+            launch_m2l_t<T>(p, d->n_m2lwork, d->m2lwork, d->geoms, d->comps, d->m2l,
+                            (const cx<T> *)d->tab, me, le, st);
+    } else {
+        launch_m2l_t<T>(p, d->n_m2lwork, d->m2lwork, d->geoms, d->comps, d->m2l,
+                        (const cx<T> *)d->tab, me, le, st);
+    }
     CK(cudaEventRecord(d->ev[3], st));
     for (int lev = 1; lev <= ctx->depth; ++lev) {
         int64_t w0 = d->gwork_off[lev], w1 = d->gwork_off[lev + 1];
@@ -650,7 +686,7 @@ lmfmm_status lmfmm_matvec_host(lmfmm_ctx *ctx, const lmfmm_c128 *J, lmfmm_c128 *
                     false));
     CK(cudaMemcpyAsync(Phi, d->stage + 3 * ctx->N, bytes, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    return LMFMM_OK;
+    return check_mvstatus(ctx);
 }
 
 lmfmm_status lmfmm_direct(lmfmm_ctx *ctx, const lmfmm_c128 *J, lmfmm_c128 *Phi, void *stream)

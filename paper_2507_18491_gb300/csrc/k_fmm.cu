@@ -78,9 +78,11 @@ static __device__ inline void sph_bessel_scaled_series(cx<T> z, cx<T> zeta, int 
 // basis b_nm(r) = scale * j_n(k |r|) Y_n^m(r^) / s^n with Y_n^m = P^_n^|m| e^{i m phi}
 // (times (-1)^m for m < 0), s = |k| S_leaf; P2M uses scale = 4 pi and conj(Y)
 // (eq. mecoeff).  FP64 form in double; mixed form in float when |k r| < 1.5.
-template <typename T>
-static __device__ inline void point_basis(int p, cd k, double dx, double dy, double dz,
-                                          bool conjugate, double scale, double inv_s, cx<T> *out)
+// visit(index n^2+n+m, b_nm) is called once per coefficient.
+template <typename T, typename Visit>
+static __device__ inline void point_basis_visit(int p, cd k, double dx, double dy, double dz,
+                                                bool conjugate, double scale, double inv_s,
+                                                Visit visit)
 {
     double r = sqrt(dx * dx + dy * dy + dz * dz);
     double rxy = sqrt(dx * dx + dy * dy);
@@ -110,11 +112,19 @@ static __device__ inline void point_basis(int p, cd k, double dx, double dy, dou
         T sg = (m & 1) ? T(-1) : T(1);
         for (int n = m; n <= p; ++n) {
             cx<T> jv = Pl[(n * (n + 1)) / 2 + m] * jn[n];
-            out[n * n + n + m] = jv * em;
-            if (m > 0) out[n * n + n - m] = sg * (jv * emc);
+            visit(n * n + n + m, jv * em);
+            if (m > 0) visit(n * n + n - m, sg * (jv * emc));
         }
         em = em * e1;
     }
+}
+
+template <typename T>
+static __device__ inline void point_basis(int p, cd k, double dx, double dy, double dz,
+                                          bool conjugate, double scale, double inv_s, cx<T> *out)
+{
+    point_basis_visit<T>(p, k, dx, dy, dz, conjugate, scale, inv_s,
+                         [&](int i, cx<T> v) { out[i] = v; });
 }
 
 template <typename T>
@@ -160,6 +170,9 @@ __global__ void k_p2m(int p, const int64_t *leaves, const BoxDev *boxes, const d
     }
 }
 
+// One CTA per leaf, one thread per target point: the basis is generated
+// coefficient by coefficient and contracted at once with the three local
+// expansions held in shared memory.
 template <typename T>
 __global__ void k_l2p(int p, const int64_t *leaves, const BoxDev *boxes, const double *xyz,
                       const cx<T> *le, MediumDev M, LayerScale ls, cd *ph)
@@ -167,24 +180,20 @@ __global__ void k_l2p(int p, const int64_t *leaves, const BoxDev *boxes, const d
     extern __shared__ unsigned char smraw[];
     const int P = (p + 1) * (p + 1);
     cx<T> *L = (cx<T> *)smraw;          // [3][P]
-    cx<T> *bas = L + 3 * P;             // [blockDim][P]
     int64_t bi = leaves[blockIdx.x];
     BoxDev b = boxes[bi];
     for (int e = threadIdx.x; e < 3 * P; e += blockDim.x) L[e] = le[bi * 3 * P + e];
     __syncthreads();
     cd k = M.k[b.layer];
     const double inv_s = 1.0 / ls.s[b.layer];
-    cx<T> *mb = bas + (size_t)threadIdx.x * P;
     for (int64_t t = b.p0 + threadIdx.x; t < b.p1; t += blockDim.x) {
-        point_basis<T>(p, k, xyz[3 * t] - b.c[0], xyz[3 * t + 1] - b.c[1], xyz[3 * t + 2] - b.c[2],
-                       false, 1.0, inv_s, mb);
         cx<T> A{T(0), T(0)}, B{T(0), T(0)}, C{T(0), T(0)};
-        for (int i = 0; i < P; ++i) {
-            cx<T> bv = mb[i];
-            A += L[i] * bv;
-            B += L[P + i] * bv;
-            C += L[2 * P + i] * bv;
-        }
+        point_basis_visit<T>(p, k, xyz[3 * t] - b.c[0], xyz[3 * t + 1] - b.c[1],
+                             xyz[3 * t + 2] - b.c[2], false, 1.0, inv_s, [&](int i, cx<T> bv) {
+                                 A += L[i] * bv;
+                                 B += L[P + i] * bv;
+                                 C += L[2 * P + i] * bv;
+                             });
         ph[3 * t] = cd{(double)A.x, (double)A.y};
         ph[3 * t + 1] = cd{(double)B.x, (double)B.y};
         ph[3 * t + 2] = cd{(double)C.x, (double)C.y};
@@ -211,7 +220,7 @@ void launch_l2p(int p, int64_t nleaf, const int64_t *leaves, const BoxDev *boxes
     if (nleaf <= 0) return;
     const int P = (p + 1) * (p + 1);
     const int thr = 64;
-    size_t sm = (size_t)(3 * P + thr * P) * sizeof(cx<T>);
+    size_t sm = (size_t)(3 * P) * sizeof(cx<T>);
     k_l2p<T><<<(unsigned)nleaf, thr, sm, st>>>(p, leaves, boxes, xyz, le, M, ls, phih);
 }
 

@@ -6,6 +6,7 @@
 // (M~_n = M_n / s^n, L~_nu = L_nu s^nu, s = |k| S_level) so that every
 // matrix entry and coefficient stays in the float range.
 #include "kernels.cuh"
+#include "m2l_cols.cuh"
 
 namespace lmf {
 
@@ -111,24 +112,6 @@ __global__ void __launch_bounds__(256) k_group_gemm(int p, const GemmWork *work,
 }
 
 // --------------------------------------------------------------------- M2L
-// Column roles per table t: (input helical v, signed kappa, coefficient,
-// output helical v) for
-//   A' = 1/2 T0[s1] a - 1/2 T2[s3] b + T1[s2] c
-//   B' = 1/2 T0[s1] b - 1/2 T-2[s3] a + T-1[s2] c
-//   C' = T0[s5] c + 1/2 T-1[s4] a + 1/2 T1[s4] b
-struct ColSpec {
-    int vin, kap;
-    double coef;
-    int vout, pad;
-};
-__constant__ ColSpec c_cols[5][2] = {
-    {{0, 0, 0.5, 0, 0}, {1, 0, 0.5, 1, 0}},     // (s1, 0)
-    {{2, 0, 1.0, 2, 0}, {2, 0, 1.0, 2, 0}},     // (s5, 0)  (one column)
-    {{2, 1, 1.0, 0, 0}, {2, -1, 1.0, 1, 0}},    // (s2, 1)
-    {{1, 1, 0.5, 2, 0}, {0, -1, 0.5, 2, 0}},    // (s4, 1)
-    {{1, 2, -0.5, 0, 0}, {0, -2, -0.5, 1, 0}},  // (s3, 2)
-};
-
 
 // The M2L of eq. M2L_scale_with_Tnmu with T = (-i)^nu i^(n'+1+d) s^(nu+mu+n'+m')
 // e^{i d phi} I-hat, d = m' - mu + kappa, factorised as
@@ -306,7 +289,7 @@ cudaError_t configure_trans_kernels()
     if ((e = cudaFuncSetAttribute(k_group_gemm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_m2l<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_m2l<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-    return cudaSuccess;
+    return configure_m2l_tc();
 }
 
 }  // namespace lmf

@@ -92,6 +92,14 @@ template <typename T>
 void launch_m2l_t(int p, int64_t nwork, const M2LWork *work, const GeomDev *geoms,
                   const CompDev *comps, const M2LPair *pairs, const cx<T> *tab, const cx<T> *me,
                   cx<T> *le, cudaStream_t st);
+// k_m2l_tc.cu: mixed-form M2L on tcgen05 tensor cores (3xTF32), p <= 15;
+// status gets bit 4 if a tensor-core wait gave up
+bool m2l_tc_supported(int p);
+int m2l_tc_cols();
+cudaError_t configure_m2l_tc();
+cudaError_t launch_m2l_tc(int p, int64_t nwork, const M2LWork *work, const GeomDev *geoms,
+                          const CompDev *comps, const M2LPair *pairs, const cf *tab, const cf *me,
+                          cf *le, int *status, cudaStream_t st);
 template <typename T>
 void launch_scale_tables(int p, int64_t g0, int64_t ng, const GeomDev *geoms, const cd *tab64,
                          cx<T> *tab, cudaStream_t st);

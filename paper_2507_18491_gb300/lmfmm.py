@@ -27,7 +27,8 @@ class C128(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int), ("depth", ctypes.c_int), ("leaf_cap", ctypes.c_int),
                 ("theta", ctypes.c_double), ("eta", ctypes.c_double),
-                ("quad_tol", ctypes.c_double), ("precision", ctypes.c_int)]
+                ("quad_tol", ctypes.c_double), ("precision", ctypes.c_int),
+                ("tensor_cores", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -37,7 +38,8 @@ class Stats(ctypes.Structure):
                 ("n_geometries", ctypes.c_int64), ("n_near_pairs", ctypes.c_int64),
                 ("n_near_point_pairs", ctypes.c_int64), ("n_quad_nodes", ctypes.c_int64),
                 ("bytes_tables", ctypes.c_double), ("ms_setup", ctypes.c_double),
-                ("ms_stage", ctypes.c_double * 8), ("m2l_columns", ctypes.c_int64)]
+                ("ms_stage", ctypes.c_double * 8), ("m2l_columns", ctypes.c_int64),
+                ("m2l_kernel", ctypes.c_int)]
 
 
 EXPORTS = ["lmfmm_default_params", "lmfmm_create", "lmfmm_set_layers", "lmfmm_set_points",
@@ -226,10 +228,11 @@ class Operator:
     setup on the GPU; ``matvec(J)`` returns A J (torch complex128, [N,3])."""
 
     def __init__(self, d, k, xyz, p=8, depth=-1, leaf_cap=64, theta=0.55, eta=0.1,
-                 precision=FP64, device=0):
+                 precision=FP64, tensor_cores=True, device=0):
         prm = default_params()
         prm.p, prm.depth, prm.leaf_cap = int(p), int(depth), int(leaf_cap)
         prm.theta, prm.eta, prm.precision = float(theta), float(eta), int(precision)
+        prm.tensor_cores = int(bool(tensor_cores))
         self.ctx = create(prm, device)
         self.N = int(np.asarray(xyz).shape[0])
         self.device = device

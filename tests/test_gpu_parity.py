@@ -210,12 +210,35 @@ def test_mixed_form_meets_its_bar():
     op64.close()
     op32 = lmfmm.Operator(w.d, w.k, w.xyz, p=10, depth=4, theta=0.5,
                           precision=lmfmm.MIXED).build()
+    assert op32.stats()["m2l_kernel"] == 2      # default: tensor-core M2L
     b = op32.matvec(Jt).cpu().numpy()
     op32.close()
     tg = rng.choice(w.N, 48, replace=False)
     ref, _ = O.direct(w.d, w.k, w.xyz, J, targets=tg, sources=src)
     assert rel(b[tg], ref) < 1e-5
     assert rel(b, a) < 2e-6
+
+
+@pytest.mark.parametrize("p", [4, 7, 8, 12, 13, 15])
+def test_tensor_core_m2l(p):
+    """Mixed form with the M2L product on the tcgen05 tensor cores (three-term
+    TF32 split) against the FP64 form, next to the FP32 SIMT product: the
+    orders cover 1 to 4 row tiles of 128 (2P = 50 ... 512)."""
+    w = W.three_layer(n=4096, p=p, depth=3)
+    Jt = torch.from_numpy(w.J).cuda()
+    kw = dict(p=p, depth=3, theta=0.5)
+    op = lmfmm.Operator(w.d, w.k, w.xyz, **kw).build()
+    a = op.matvec(Jt).cpu().numpy()
+    op.close()
+    out = {}
+    for tc in (True, False):
+        op = lmfmm.Operator(w.d, w.k, w.xyz, precision=lmfmm.MIXED, tensor_cores=tc, **kw).build()
+        assert op.stats()["m2l_kernel"] == (2 if tc else 1)
+        out[tc] = op.matvec(Jt).cpu().numpy()
+        op.close()
+    e_tc, e_simt = rel(out[True], a), rel(out[False], a)
+    print("p=%d tensor cores %.3e  SIMT %.3e" % (p, e_tc, e_simt))
+    assert e_tc < 5e-6 and e_tc < 3 * e_simt + 1e-7
 
 
 def test_stats_before_first_matvec():
