@@ -64,9 +64,11 @@ typedef struct {
     double eta;        /* ... and its vertical transmission distance is >= eta * |c_s - c_t| */
     double quad_tol;   /* relative cut-off of the k_rho tails (>= 1e-16) */
     int precision;     /* LMFMM_FP64 or LMFMM_MIXED (FP32 translation arithmetic) */
-    int tensor_cores;  /* mixed form only: 1 runs the M2L products on the tcgen05 tensor cores
-                          (FP32 accuracy by a three-term TF32 split; p <= 15), 0 on the
-                          FP32 SIMT pipes.  Ignored by the FP64 form. */
+    int tensor_cores;  /* mixed form only: M2L products on the tcgen05 tensor cores with FP32
+                          accuracy from a three-term TF32 split.  1: the persistent kernel on a
+                          pre-tiled table image for p <= 13, else the streamed-operand kernel
+                          (p <= 15); 2: the streamed-operand kernel; 0: FP32 SIMT pipes.
+                          Beyond p = 15 the SIMT kernel runs.  Ignored by the FP64 form. */
 } lmfmm_params;
 
 typedef struct {
@@ -80,12 +82,12 @@ typedef struct {
     int64_t n_near_pairs;  /* near box pairs */
     int64_t n_near_point_pairs;
     int64_t n_quad_nodes;  /* k_rho nodes summed over all tabulated geometries */
-    double bytes_tables;   /* device bytes held by M2L tables */
+    double bytes_tables;   /* device bytes held by M2L tables (or their tiled TF32 image) */
     double ms_setup;       /* wall time of the last lmfmm_build */
     double ms_stage[8];    /* last matvec: P2M, M2M, M2L, L2L, L2P, S2T, permute, total */
     int64_t m2l_columns;   /* helical columns pushed through M2L tables per matvec */
     int m2l_kernel;        /* M2L product of the built form: 0 FP64 SIMT, 1 FP32 SIMT,
-                              2 tcgen05 tensor cores (three-term TF32) */
+                              2 tcgen05 streamed-operand kernel, 3 tcgen05 persistent kernel */
 } lmfmm_stats;
 
 /* Fill *prm with defaults (p = 8, depth from leaf_cap = 64, theta = 0.55,

@@ -42,7 +42,10 @@ struct DevState {
     cd *s2t = nullptr;
     int *flag = nullptr;
     int *mvstatus = nullptr;         // matvec status word (bit 4: tensor-core wait gave up)
-    bool m2l_tc = false;             // mixed-form M2L on the tcgen05 tensor cores
+    int m2l_kernel = 0;              // 0 FP64 SIMT, 1 FP32 SIMT, 2 tcgen05 streamed, 3 tcgen05 persistent
+    float *yscr = nullptr;           // persistent kernel: per-CTA accumulator scratch
+    cf *ephase = nullptr;            // persistent kernel: e^{i d phi} per pair, d = -(p+2)..p+2
+    int nsm = 0;
     cd *stage = nullptr;             // [2][N][3] for host-buffer matvec
     cudaEvent_t ev[9]{};
     bool ev_ok = false;
@@ -278,8 +281,8 @@ lmfmm_status lmfmm_create(lmfmm_ctx **out, const lmfmm_params *prm, int device)
         g_err = "lmfmm_create: precision must be LMFMM_FP64 or LMFMM_MIXED";
         return LMFMM_ERR_ARG;
     }
-    if (prm->tensor_cores != 0 && prm->tensor_cores != 1) {
-        g_err = "lmfmm_create: tensor_cores must be 0 or 1";
+    if (prm->tensor_cores < 0 || prm->tensor_cores > 2) {
+        g_err = "lmfmm_create: tensor_cores must be 0, 1 or 2";
         return LMFMM_ERR_ARG;
     }
     cudaError_t e = cudaSetDevice(device);
@@ -365,7 +368,12 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
     const int p = ctx->prm.p, P = (p + 1) * (p + 1);
     const int64_t N = ctx->N, nbox = (int64_t)ctx->boxes.size();
     // memory estimate (tables dominate)
+    const bool img_path = ctx->prm.precision == LMFMM_MIXED && ctx->prm.tensor_cores == 1 &&
+                          m2l_tc2_supported(p);
     double need = (double)ctx->geoms.size() * NTAB * P * P * 16.0 +
+                  (img_path ? (double)m2l_tc2_image_bytes(p, (int64_t)ctx->geoms.size()) +
+                                  (double)ctx->m2l.size() * (2 * p + 5) * 8.0
+                            : 0.0) +
                   (double)nbox * 6 * P * 16.0 + (double)ctx->tgroups.size() * 2 * P * P * 16.0 +
                   (double)ctx->n_near_pp * 5 * 16.0 + (double)N * 200.0;
     size_t fr = 0, tot = 0;
@@ -399,7 +407,10 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
     TRY(dalloc(ctx, &d->qh, 3 * N));
     TRY(dalloc(ctx, &d->ph, 3 * N));
     const bool f32 = ctx->prm.precision == LMFMM_MIXED;
-    d->m2l_tc = f32 && ctx->prm.tensor_cores && m2l_tc_supported(p);
+    d->m2l_kernel = !f32 ? 0
+                    : ctx->prm.tensor_cores == 0 ? 1
+                    : (ctx->prm.tensor_cores == 1 && m2l_tc2_supported(p)) ? 3
+                    : m2l_tc_supported(p) ? 2 : 1;
     const size_t esz = f32 ? sizeof(cf) : sizeof(cd);
     {
         unsigned char *q1 = nullptr, *q2 = nullptr;
@@ -448,7 +459,32 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
         TRY(dalloc(ctx, &tab64, ctx->geoms.size() * (size_t)NTAB * P * P));
         TRY(tabulate(ctx, hg, d->comps, dG, dcg, tab64, st));
         TRY(dupload(ctx, &d->geoms, hg));
-        if (f32) {
+        if (d->m2l_kernel == 3) {
+            float *img = nullptr;
+            TRY(dalloc(ctx, &img, m2l_tc2_image_bytes(p, (int64_t)hg.size()) / sizeof(float)));
+            launch_tile_tables(p, 0, (int64_t)hg.size(), d->geoms, d->comps, tab64, img, st);
+            CK(cudaGetLastError());
+            CK(cudaStreamSynchronize(st));
+            dfree(ctx, tab64);
+            d->tab = img;
+            CK(cudaDeviceGetAttribute(&d->nsm, cudaDevAttrMultiProcessorCount, ctx->device));
+            TRY(dalloc(ctx, &d->yscr, m2l_tc2_scratch_floats(p, d->nsm)));
+            // phases of every pair: powers in FP64, rounded once to FP32
+            const int MW = 2 * p + 5;
+            std::vector<cf> ph(ctx->m2l.size() * (size_t)MW);
+            for (size_t i = 0; i < ctx->m2l.size(); ++i) {
+                const cd b{ctx->m2l[i].cphi, ctx->m2l[i].sphi};
+                cd e{1.0, 0.0};
+                cf *row = ph.data() + i * MW + (p + 2);
+                row[0] = cf{1.f, 0.f};
+                for (int m = 1; m <= p + 2; ++m) {
+                    e = e * b;
+                    row[m] = cf{(float)e.x, (float)e.y};
+                    row[-m] = cf{(float)e.x, (float)-e.y};
+                }
+            }
+            TRY(dupload(ctx, &d->ephase, ph));
+        } else if (f32) {
             cf *t32 = nullptr;
             TRY(dalloc(ctx, &t32, ctx->geoms.size() * (size_t)NTAB * P * P));
             launch_scale_tables<float>(p, 0, (int64_t)hg.size(), d->geoms, tab64, t32, st);
@@ -468,7 +504,7 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
     for (size_t gi = 0; gi < ctx->geoms.size(); ++gi) {
         const Geom &g = ctx->geoms[gi];
         for (int t = 0; t < NTAB; ++t) {
-            int bn = d->m2l_tc ? m2l_tc_cols() : f32 ? gemm_cols<float>() : gemm_cols<double>();
+            int bn = d->m2l_kernel >= 2 ? m2l_tc_cols() : f32 ? gemm_cols<float>() : gemm_cols<double>();
             int per = (t == 1) ? bn : bn / 2;
             for (int64_t q = g.pair0; q < g.pair1; q += per) {
                 M2LWork w{};
@@ -567,10 +603,11 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
     S.n_near_pairs = (int64_t)ctx->near.size();
     S.n_near_point_pairs = ctx->n_near_pp;
     S.n_quad_nodes = qtot;
-    S.bytes_tables = (double)ctx->geoms.size() * NTAB * P * P * 16.0;
+    S.bytes_tables = d->m2l_kernel == 3 ? (double)m2l_tc2_image_bytes(p, (int64_t)ctx->geoms.size())
+                     : (double)ctx->geoms.size() * NTAB * P * P * (f32 ? 8.0 : 16.0);
     S.ms_setup = std::chrono::duration<double, std::milli>(t1 - t0).count();
     S.m2l_columns = ncols;
-    S.m2l_kernel = d->m2l_tc ? 2 : f32 ? 1 : 0;
+    S.m2l_kernel = d->m2l_kernel;
     return LMFMM_OK;
 }
 
@@ -597,7 +634,10 @@ static lmfmm_status matvec_t(lmfmm_ctx *ctx, const lmfmm_c128 *J, lmfmm_c128 *Ph
     CK(cudaEventRecord(d->ev[2], st));
     CK(cudaMemsetAsync(le, 0, (size_t)nbox * 3 * P * sizeof(cx<T>), st));
     if constexpr (std::is_same<T, float>::value) {
-        if (d->m2l_tc)
+        if (d->m2l_kernel == 3)
+            CK(launch_m2l_tc2(p, d->n_m2lwork, d->m2lwork, d->geoms, d->comps, d->m2l,
+                              d->ephase, (const float *)d->tab, me, le, d->yscr, d->nsm, d->mvstatus, st));
+        else if (d->m2l_kernel == 2)
             CK(launch_m2l_tc(p, d->n_m2lwork, d->m2lwork, d->geoms, d->comps, d->m2l,
                              (const cf *)d->tab, me, le, d->mvstatus, st));
         else

@@ -26,6 +26,8 @@
 // the accumulator with tcgen05.ld, pairs the Re/Im rows with one shuffle,
 // applies the output factors of the M2L and adds into the local expansion
 // with float2 atomics.
+#include <algorithm>
+
 #include "kernels.cuh"
 #include "m2l_cols.cuh"
 #include "tc.cuh"
@@ -355,6 +357,434 @@ __global__ void __launch_bounds__(NT) k_m2l_tc(int p, int MT, uint32_t tmem_cols
     if (warp == 0) tc::tmem_dealloc(tbase, tmem_cols);
 }
 
+// ====================================================================== v2
+// Persistent, warp-specialised form with the operand roles exchanged:
+//   D (128 x NR) = X (128 x K) T'^T,
+// whose 128 rows are real columns -- rows 2c, 2c+1 hold (Re x, -Im x) and
+// (Im x, Re x) of complex column c, giving Re (T' x) and Im (T' x) -- and
+// whose NR >= P columns are the table rows (nu, mu).  The table enters as
+// the B operand unchanged in shape (K = interleaved Re/Im input index); it
+// is stored once per build as TF32 hi/lo planes in exactly the shared-memory
+// image of each K-chunk, with the factors of the M2L that depend only on the
+// degrees folded in:
+//   T'[nu mu][n' m'] = (-i)^nu f_t^nu  T[nu mu][n' m']  i^n' f_s^n'
+// (f = -1 where a downward component or a mirrored box flips odd powers,
+// else 1; these are exact in any precision).  What is left per column is one
+// complex factor per input order m' (phase e^{i m' phi} and i^m') and one per
+// output order mu.  Roles (320 threads, one CTA per SM):
+//   warps 0-3  X producers: the work item's 64 columns, coefficients
+//              prefetched V2_D chunks ahead, split into TF32 hi/lo and written
+//              into a V2_SX-slot tensor-memory ring (A operand);
+//   warps 4-7  epilogue: accumulators -> a per-CTA scratch in global memory
+//              (L2-resident; tensor memory is free for the next item at once),
+//              then the output factors and float2 atomics into the local
+//              expansions;
+//   warp 8     one bulk copy per table chunk into an S_T-slot shared ring;
+//   warp 9     MMA issue: A_hi B_hi into one accumulator, A_hi B_lo + A_lo B_hi
+//              into a second (the tensor core truncates small addends against a
+//              large accumulator).
+// Every wait is bounded; a wait that gives up sets bit 4 of the status word
+// and its role stops.
+namespace {
+
+constexpr int V2_SX = 6;           // X ring slots (tensor memory, 16 columns each)
+constexpr int V2_ST_MAX = 16;      // table ring slots (shared memory)
+constexpr int V2_D = 8;            // coefficient chunks prefetched into registers
+constexpr int V2_NR_MAX = 208;     // table rows padded to 16: p <= 13
+constexpr int V2_THREADS = 320;
+constexpr uint32_t V2_SMEM_MAX = 227 * 1024;
+
+struct V2Col {
+    int64_t in_base, out_base;   // (box * 3 + helical v) * P of the source / target
+    int pp, kap;                 // pair within the work item, signed kappa
+};
+
+struct V2Plan {
+    uint32_t NR, nchunk, CB, ST, MO, g_bytes, meta_bytes, meta, tabs, bars, total;
+};
+
+__host__ __device__ inline V2Plan v2_plan(int p)
+{
+    const int P = (p + 1) * (p + 1);
+    V2Plan s;
+    s.NR = (uint32_t)((P + 15) & ~15);
+    s.nchunk = (uint32_t)((P + 3) / 4);
+    s.CB = s.NR * 64;                               // hi + lo image of a chunk: NR rows x 8 tf32 x 2
+    s.MO = 2 * p + 1;                               // orders -p..p
+    s.g_bytes = BN * s.MO * 8;                      // one factor table: [64][2p+1] complex
+    s.meta_bytes = 2 * s.g_bytes + BN * (uint32_t)sizeof(V2Col);
+    const uint32_t fixed = 2 * s.meta_bytes + 4 * P + 16 + (2 * V2_ST_MAX + 2 * V2_SX + 12) * 8 + 16;
+    uint32_t st = (V2_SMEM_MAX - fixed) / s.CB;
+    s.ST = st > V2_ST_MAX ? V2_ST_MAX : st;
+    s.meta = s.ST * s.CB;
+    s.tabs = s.meta + 2 * s.meta_bytes;
+    s.bars = (s.tabs + 4 * P + 15) & ~15u;
+    s.total = s.bars + (2 * V2_ST_MAX + 2 * V2_SX + 12) * 8 + 16;
+    return s;
+}
+
+// i^k v, exact
+__device__ __forceinline__ cf mul_ipow(int k, cf v)
+{
+    switch (k & 3) {
+    case 0: return v;
+    case 1: return cf{-v.y, v.x};
+    case 2: return cf{-v.x, -v.y};
+    default: return cf{v.y, -v.x};
+    }
+}
+
+// per-item column data, all exact transforms of the pair phases
+// E[pp][d] = e^{i d phi} (FP64-computed, stored FP32):
+//   input factors  G[pp][m'] = i^m' f_s^m' E[m'],
+//   output factors O[col][mh] = coef i^(1+kappa) (-i)^mu f_t^mu E[kappa - mu],
+//   mu = +-mh (sign of kappa), coef in {1/2, 1, -1/2};
+// and the column records
+__device__ __forceinline__ void v2_fill_meta(int p, int P, const M2LWork &w, const M2LPair *pairs,
+                                             const cf *ephase, bool flip_in, bool flip_out, cf *G, cf *O,
+                                             V2Col *cols, int j, int nthr)
+{
+    const int MO = 2 * p + 1, MW = 2 * p + 5;
+    const int t = w.t, ncpp = (t == 1) ? 1 : 2, ncol = w.npair * ncpp;
+    for (int e = j; e < w.npair * MO; e += nthr) {
+        const int pp = e / MO, m = e % MO - p;
+        cf v = mul_ipow(m, ephase[(w.pair0 + pp) * MW + (p + 2) + m]);
+        if (flip_in && (m & 1)) v = -v;
+        G[pp * MO + p + m] = v;
+    }
+    for (int e = j; e < ncol * MO; e += nthr) {
+        const int col = e / MO, mh = e % MO - p;
+        const int pp = col / ncpp;
+        const ColSpec cs = c_cols[t][col % ncpp];
+        const int mu = cs.kap < 0 ? -mh : mh;
+        float cf0 = (float)cs.coef;
+        if (cs.kap < 0 && (cs.kap & 1)) cf0 = -cf0;
+        cf v = mul_ipow(1 + cs.kap - mu, ephase[(w.pair0 + pp) * MW + (p + 2) + cs.kap - mu]);
+        if (flip_out && (mu & 1)) cf0 = -cf0;
+        O[col * MO + p + mh] = cf0 * v;
+    }
+    for (int col = j; col < BN; col += nthr) {
+        V2Col q{};
+        if (col < ncol) {
+            const int pp = col / ncpp;
+            const ColSpec cs = c_cols[t][col % ncpp];
+            const M2LPair pr = pairs[w.pair0 + pp];
+            q.in_base = (pr.src * 3 + cs.vin) * (int64_t)P;
+            q.out_base = (pr.tgt * 3 + cs.vout) * (int64_t)P;
+            q.pp = pp;
+            q.kap = cs.kap;
+        }
+        cols[col] = q;
+    }
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(V2_THREADS, 1)
+    k_m2l_tc2(int p, int64_t nwork, const M2LWork *work, const GeomDev *geoms, const CompDev *comps,
+              const M2LPair *pairs, const cf *ephase, const float *timg, const cf *me, cf *le, float *yscr,
+              int *status)
+{
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    const int P = (p + 1) * (p + 1);
+    const V2Plan sp = v2_plan(p);
+    const int NR = (int)sp.NR, nchunk = (int)sp.nchunk, ST = (int)sp.ST, MO = (int)sp.MO;
+    short *DEG = (short *)(smraw + sp.tabs), *MM = DEG + P;   // degree n and order m of index k
+    uint64_t *bars = (uint64_t *)(smraw + sp.bars);
+    uint64_t *tfull = bars, *tempty = bars + V2_ST_MAX, *xfull = bars + 2 * V2_ST_MAX,
+             *xempty = xfull + V2_SX;
+    uint64_t *accfull = xempty + V2_SX, *accempty = accfull + 1, *metafull = accfull + 2,
+             *metaempty = accfull + 4, *fin = accfull + 6, *ydone = accfull + 7, *yfree = accfull + 8;
+    uint32_t *tslot = (uint32_t *)(accfull + 9);
+    auto meta_G = [&](int slot) { return (cf *)(smraw + sp.meta + slot * sp.meta_bytes); };
+    auto meta_O = [&](int slot) { return (cf *)(smraw + sp.meta + slot * sp.meta_bytes + sp.g_bytes); };
+    auto meta_cols = [&](int slot) {
+        return (V2Col *)(smraw + sp.meta + slot * sp.meta_bytes + 2 * sp.g_bytes);
+    };
+    float *Y = yscr + (size_t)blockIdx.x * NR * 128;   // [r][real column]
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t XB = 2 * (uint32_t)NR;              // tensor-memory column of the X ring
+
+    if (warp == 0) tc::tmem_alloc(tslot, 512);
+    if (tid == 0) {
+        for (int s = 0; s < ST; ++s) {
+            tc::mbar_init(&tfull[s], 1);
+            tc::mbar_init(&tempty[s], 1);
+        }
+        for (int s = 0; s < V2_SX; ++s) {
+            tc::mbar_init(&xfull[s], 128);
+            tc::mbar_init(&xempty[s], 1);
+        }
+        tc::mbar_init(accfull, 1);
+        tc::mbar_init(accempty, 128);
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&metafull[i], 128);
+            tc::mbar_init(&metaempty[i], 128);
+        }
+        tc::mbar_init(fin, 1);
+        tc::mbar_init(ydone, 128);
+        tc::mbar_init(yfree, 128);
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    for (int k = tid; k < P; k += V2_THREADS) {
+        int n = (int)sqrtf((float)k + 0.5f);
+        while ((n + 1) * (n + 1) <= k) ++n;
+        while (n * n > k) --n;
+        DEG[k] = (short)n;
+        MM[k] = (short)(k - n * n - n);
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tbase = *tslot;
+    bool failed = false;
+
+    if (warp == 8) {
+        // ------------------------------------------------ table chunks
+        if (lane == 0) {
+            uint32_t g = 0;
+            for (int64_t it = blockIdx.x; it < nwork && !failed; it += gridDim.x) {
+                const M2LWork w = work[it];
+                const int64_t ti = geoms[w.geom].tab_index * NTAB + w.t;
+                const unsigned char *src = (const unsigned char *)timg + (size_t)ti * nchunk * sp.CB;
+                for (int c = 0; c < nchunk; ++c, ++g) {
+                    const int s = g % ST;
+                    if (g >= (uint32_t)ST && !tc::mbar_wait(&tempty[s], ((g / ST) - 1) & 1, WAIT_POLLS)) {
+                        failed = true;
+                        break;
+                    }
+                    tc::mbar_expect_tx(&tfull[s], sp.CB);
+                    tc::bulk_g2s(smraw + s * sp.CB, src + (size_t)c * sp.CB, sp.CB, &tfull[s]);
+                }
+            }
+            // copies still in flight land before the CTA leaves
+            for (uint32_t q = g > (uint32_t)ST ? g - ST : 0; q < g; ++q)
+                tc::mbar_wait(&tfull[q % ST], (q / ST) & 1, WAIT_POLLS);
+        }
+    } else if (warp == 9) {
+        // ------------------------------------------------ MMA issue
+        if (lane == 0) {
+            const uint32_t idesc = tc::idesc_tf32(128, NR, false);
+            uint32_t g = 0, li = 0;
+            for (int64_t it = blockIdx.x; it < nwork && !failed; it += gridDim.x, ++li) {
+                if (li >= 1 && !tc::mbar_wait(accempty, (li - 1) & 1, WAIT_POLLS)) {
+                    failed = true;
+                    break;
+                }
+                tc::fence_after();
+                for (int c = 0; c < nchunk; ++c, ++g) {
+                    const int st = g % ST, sx = g % V2_SX;
+                    if (!tc::mbar_wait(&tfull[st], (g / ST) & 1, WAIT_POLLS) ||
+                        !tc::mbar_wait(&xfull[sx], (g / V2_SX) & 1, WAIT_POLLS)) {
+                        failed = true;
+                        break;
+                    }
+                    tc::fence_after();
+                    const uint32_t ahi = tbase + XB + 16 * sx, alo = ahi + 8;
+                    const uint32_t bhi = tc::smem_u32(smraw + st * sp.CB), blo = bhi + NR * 32;
+                    const uint64_t dbh = tc::sdesc(bhi, 128, 256), dbl = tc::sdesc(blo, 128, 256);
+                    tc::mma_tf32_ta(tbase, ahi, dbh, idesc, c > 0 ? 1u : 0u);
+                    tc::mma_tf32_ta(tbase + NR, ahi, dbl, idesc, c > 0 ? 1u : 0u);
+                    tc::mma_tf32_ta(tbase + NR, alo, dbh, idesc, 1u);
+                    tc::commit(&tempty[st]);
+                    tc::commit(&xempty[sx]);
+                }
+                if (failed) break;
+                tc::commit(accfull);
+            }
+            tc::commit(fin);   // every MMA issued above has completed once fin flips
+            tc::mbar_wait(fin, 0, WAIT_POLLS);
+        }
+    } else if (warp < 4) {
+        // ------------------------------------------------ X producers
+        const int j = tid, cc = j >> 1, b = j & 1;
+        const uint32_t lane_base = tbase + ((uint32_t)(32 * warp) << 16);
+        uint32_t g = 0, li = 0;
+        for (int64_t it = blockIdx.x; it < nwork && !failed; it += gridDim.x, ++li) {
+            const int slot = li & 1;
+            cf *G = meta_G(slot);
+            V2Col *cols = meta_cols(slot);
+            const M2LWork w = work[it];
+            const CompDev c = comps[geoms[w.geom].comp];
+            const bool flip_in = (c.s < 0) != (c.has_src_refl != 0);
+            const bool flip_out = (c.s < 0) != (c.has_tgt_refl != 0);
+            bool ok = li < 2 || tc::mbar_wait(&metaempty[slot], ((li >> 1) - 1) & 1, WAIT_POLLS);
+            if (ok) {
+                v2_fill_meta(p, P, w, pairs, ephase, flip_in, flip_out, G, meta_O(slot), cols, j, 128);
+                tc::mbar_arrive(&metafull[slot]);
+                ok = tc::mbar_wait(&metafull[slot], (li >> 1) & 1, WAIT_POLLS);
+            }
+            if (__any_sync(0xffffffffu, !ok)) {
+                failed = true;
+                break;
+            }
+            const int ncol = w.npair * ((w.t == 1) ? 1 : 2);
+            const bool valid = cc < ncol;
+            V2Col q{};
+            if (valid) q = cols[cc];
+            const bool neg = q.kap < 0;
+            const cf *gr = G + q.pp * MO + p;
+            const cf *src = me + q.in_base;
+            float2 pre[V2_D][4];
+            // input (n', m') reads the expansion at (n', +-m'): index k or k - 2m'
+            auto fetch = [&](int ch, float2(&v)[4]) {
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const int k = 4 * ch + h;
+                    float2 x = make_float2(0.f, 0.f);
+                    if (valid && k < P) x = *(const float2 *)(src + (neg ? k - 2 * MM[k] : k));
+                    v[h] = x;
+                }
+            };
+#pragma unroll
+            for (int u = 0; u < V2_D; ++u)
+                if (u < nchunk) fetch(u, pre[u]);
+            for (int c0 = 0; c0 < nchunk && !failed; c0 += V2_D) {
+#pragma unroll
+                for (int u = 0; u < V2_D; ++u) {
+                    const int ch = c0 + u;
+                    if (ch >= nchunk) break;
+                    const int s = g % V2_SX;
+                    bool okw = g < (uint32_t)V2_SX || tc::mbar_wait(&xempty[s], ((g / V2_SX) - 1) & 1, WAIT_POLLS);
+                    if (__any_sync(0xffffffffu, !okw)) {
+                        failed = true;
+                        break;
+                    }
+                    tc::fence_after();
+                    uint32_t hi[8], lo[8];
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        const int k = 4 * ch + h;
+                        float yr = 0.f, yi = 0.f;
+                        if (valid && k < P) {
+                            const int m = MM[k];
+                            const cf y = gr[neg ? -m : m] * cf{pre[u][h].x, pre[u][h].y};
+                            yr = y.x;
+                            yi = y.y;
+                        }
+                        const float a0 = b ? yi : yr, a1 = b ? yr : -yi;
+                        const float h0 = tc::tf32_round(a0), h1 = tc::tf32_round(a1);
+                        hi[2 * h] = __float_as_uint(h0);
+                        hi[2 * h + 1] = __float_as_uint(h1);
+                        lo[2 * h] = __float_as_uint(tc::tf32_round(a0 - h0));
+                        lo[2 * h + 1] = __float_as_uint(tc::tf32_round(a1 - h1));
+                    }
+                    tc::tmem_st8(lane_base + XB + 16 * s, hi);
+                    tc::tmem_st8(lane_base + XB + 16 * s + 8, lo);
+                    tc::tmem_st_wait();
+                    tc::fence_before();
+                    tc::mbar_arrive(&xfull[s]);
+                    ++g;
+                    if (ch + V2_D < nchunk) fetch(ch + V2_D, pre[u]);
+                }
+            }
+        }
+    } else {
+        // ------------------------------------------------ epilogue
+        const int e = tid - 128, q4 = warp & 3;
+        const uint32_t lane_base = tbase + ((uint32_t)(32 * q4) << 16);
+        uint32_t li = 0;
+        for (int64_t it = blockIdx.x; it < nwork && !failed; it += gridDim.x, ++li) {
+            const int slot = li & 1;
+            bool ok = tc::mbar_wait(accfull, li & 1, WAIT_POLLS);
+            if (ok && li >= 1) ok = tc::mbar_wait(yfree, (li - 1) & 1, WAIT_POLLS);
+            if (__any_sync(0xffffffffu, !ok)) {
+                failed = true;
+                break;
+            }
+            tc::fence_after();
+            for (int c0 = 0; c0 < NR; c0 += 16) {   // NR is a multiple of 16
+                uint32_t va[16], vb[16];
+                tc::tmem_ld16(lane_base + c0, va);
+                tc::tmem_ld16(lane_base + NR + c0, vb);
+                tc::tmem_ld_wait();
+#pragma unroll
+                for (int i = 0; i < 16; ++i)
+                    Y[(size_t)(c0 + i) * 128 + e] = __uint_as_float(va[i]) + __uint_as_float(vb[i]);
+            }
+            tc::fence_before();
+            tc::mbar_arrive(accempty);
+            tc::mbar_arrive(ydone);
+            ok = tc::mbar_wait(ydone, li & 1, WAIT_POLLS) &&
+                 tc::mbar_wait(&metafull[slot], (li >> 1) & 1, WAIT_POLLS);
+            if (!ok) {
+                failed = true;
+                break;
+            }
+            const M2LWork w = work[it];
+            const int ncol = w.npair * ((w.t == 1) ? 1 : 2);
+            const cf *O = meta_O(slot);
+            const V2Col *cols = meta_cols(slot);
+            int cc = 0, r = e;
+            while (r >= P) {
+                r -= P;
+                ++cc;
+            }
+            while (cc < ncol) {
+                const V2Col &cq = cols[cc];
+                const float2 y = *(const float2 *)(Y + (size_t)r * 128 + 2 * cc);
+                const int mh = MM[r];
+                const cf yy = O[cc * MO + p + mh] * cf{y.x, y.y};
+                // output (nu, mu) with mu = +-mh: index r or r - 2 mh
+                atomicAdd((float2 *)(le + cq.out_base + (cq.kap < 0 ? r - 2 * mh : r)), make_float2(yy.x, yy.y));
+                r += 128;
+                while (r >= P) {
+                    r -= P;
+                    ++cc;
+                }
+            }
+            tc::mbar_arrive(yfree);
+            tc::mbar_arrive(&metaempty[slot]);
+        }
+    }
+    if (failed) atomicOr(status, 4);
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tbase, 512);
+}
+
+// table image of the persistent kernel: per (geometry, table) nchunk chunks,
+// each the TF32 hi plane then the lo plane of NR rows x 8 real K in the
+// canonical K-major layout, from the FP64 table with the level scaling
+// s_t^nu s_s^n' and the degree factors (-i)^nu f_t^nu, i^n' f_s^n' applied
+// before the split
+__global__ void k_tile_tables(int p, int64_t g0, int64_t ng, const GeomDev *geoms, const CompDev *comps,
+                              const cd *tab64, float *img)
+{
+    const int P = (p + 1) * (p + 1);
+    const V2Plan sp = v2_plan(p);
+    const int NR = (int)sp.NR;
+    const int64_t gi = g0 + blockIdx.y;
+    const int t = blockIdx.z;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int)sp.nchunk * NR * 8 || gi >= g0 + ng) return;
+    const int c = e / (NR * 8), rem = e % (NR * 8), r = rem >> 3, kk = rem & 7;
+    const int k = 4 * c + (kk >> 1);
+    const GeomDev &g = geoms[gi];
+    double v = 0.0;
+    if (r < P && k < P) {
+        int nu = (int)sqrt((double)r + 0.5), n1 = (int)sqrt((double)k + 0.5);
+        while ((nu + 1) * (nu + 1) <= r) ++nu;
+        while (nu * nu > r) --nu;
+        while ((n1 + 1) * (n1 + 1) <= k) ++n1;
+        while (n1 * n1 > k) --n1;
+        const CompDev cp = comps[g.comp];
+        const bool flip_in = (cp.s < 0) != (cp.has_src_refl != 0);
+        const bool flip_out = (cp.s < 0) != (cp.has_tgt_refl != 0);
+        const double f = pow(g.scale_t, (double)nu) * pow(g.scale_s, (double)n1) *
+                         ((flip_in && (n1 & 1)) ? -1.0 : 1.0) * ((flip_out && (nu & 1)) ? -1.0 : 1.0);
+        const cd a = tab64[((gi - g0) * NTAB + t) * (int64_t)P * P + (int64_t)r * P + k];
+        const cd s = ipow<double>(n1 - nu) * (f * a);   // i^n' (-i)^nu = i^(n' - nu)
+        v = (kk & 1) ? s.y : s.x;
+    }
+    const float hi = tc::tf32_round((float)v);
+    const float lo = tc::tf32_round((float)(v - (double)hi));
+    const size_t base = ((size_t)(g.tab_index * NTAB + t) * sp.nchunk + c) * (size_t)(NR * 16);
+    const int off = ((r >> 3) * 256 + (kk >> 2) * 128 + (r & 7) * 16 + (kk & 3) * 4) >> 2;
+    img[base + off] = hi;
+    img[base + NR * 8 + off] = lo;
+}
+
 namespace {
 int tc_mtiles(int p) { return (2 * (p + 1) * (p + 1) + 127) / 128; }
 uint32_t tc_tmem_cols(int MT)
@@ -388,9 +818,45 @@ cudaError_t launch_m2l_tc(int p, int64_t nwork, const M2LWork *work, const GeomD
     return cudaGetLastError();
 }
 
+bool m2l_tc2_supported(int p) { return p >= 1 && v2_plan(p).NR <= (uint32_t)V2_NR_MAX && v2_plan(p).ST >= 4; }
+
+size_t m2l_tc2_image_bytes(int p, int64_t ngeom)
+{
+    const V2Plan sp = v2_plan(p);
+    return (size_t)ngeom * NTAB * sp.nchunk * sp.CB;
+}
+
+size_t m2l_tc2_scratch_floats(int p, int nsm) { return (size_t)nsm * 128 * v2_plan(p).NR; }
+
+void launch_tile_tables(int p, int64_t g0, int64_t ng, const GeomDev *geoms, const CompDev *comps,
+                        const cd *tab64, float *img, cudaStream_t st)
+{
+    if (ng <= 0) return;
+    const V2Plan sp = v2_plan(p);
+    dim3 grid((sp.nchunk * sp.NR * 8 + 255) / 256, (unsigned)ng, NTAB);
+    k_tile_tables<<<grid, 256, 0, st>>>(p, g0, ng, geoms, comps, tab64, img);
+}
+
+cudaError_t launch_m2l_tc2(int p, int64_t nwork, const M2LWork *work, const GeomDev *geoms,
+                           const CompDev *comps, const M2LPair *pairs, const cf *ephase, const float *img,
+                           const cf *me, cf *le, float *yscr, int nsm, int *status, cudaStream_t st)
+{
+    if (nwork <= 0) return cudaSuccess;
+    if (!m2l_tc2_supported(p) || nsm < 1) return cudaErrorInvalidValue;
+    const int64_t grid = std::min<int64_t>(nwork, (int64_t)nsm);
+    // each CTA takes all 512 tensor-memory columns: ask for more than half of
+    // an SM's shared memory so that no two CTAs are resident on one SM
+    const size_t smem = std::max<size_t>(v2_plan(p).total, 116 * 1024);
+    k_m2l_tc2<<<(unsigned)grid, V2_THREADS, smem, st>>>(p, nwork, work, geoms, comps, pairs, ephase, img, me,
+                                                        le, yscr, status);
+    return cudaGetLastError();
+}
+
 cudaError_t configure_m2l_tc()
 {
-    return cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_m2l_tc2, cudaFuncAttributeMaxDynamicSharedMemorySize, V2_SMEM_MAX);
 }
 
 }  // namespace lmf

@@ -100,6 +100,19 @@ cudaError_t configure_m2l_tc();
 cudaError_t launch_m2l_tc(int p, int64_t nwork, const M2LWork *work, const GeomDev *geoms,
                           const CompDev *comps, const M2LPair *pairs, const cf *tab, const cf *me,
                           cf *le, int *status, cudaStream_t st);
+// persistent warp-specialised variant (p <= 13) on a pre-tiled TF32 hi/lo
+// table image written by launch_tile_tables from the FP64 tables; ephase
+// holds e^{i d phi} of every pair, d = -(p+2)..p+2 ([npair][2p+5], FP32 from
+// FP64); yscr holds m2l_tc2_scratch_floats(p, nsm) floats, nsm = CTAs of the
+// launch (the SM count)
+bool m2l_tc2_supported(int p);
+size_t m2l_tc2_image_bytes(int p, int64_t ngeom);
+size_t m2l_tc2_scratch_floats(int p, int nsm);
+void launch_tile_tables(int p, int64_t g0, int64_t ng, const GeomDev *geoms, const CompDev *comps,
+                        const cd *tab64, float *img, cudaStream_t st);
+cudaError_t launch_m2l_tc2(int p, int64_t nwork, const M2LWork *work, const GeomDev *geoms,
+                           const CompDev *comps, const M2LPair *pairs, const cf *ephase, const float *img,
+                           const cf *me, cf *le, float *yscr, int nsm, int *status, cudaStream_t st);
 template <typename T>
 void launch_scale_tables(int p, int64_t g0, int64_t ng, const GeomDev *geoms, const cd *tab64,
                          cx<T> *tab, cudaStream_t st);

@@ -232,7 +232,7 @@ class Operator:
         prm = default_params()
         prm.p, prm.depth, prm.leaf_cap = int(p), int(depth), int(leaf_cap)
         prm.theta, prm.eta, prm.precision = float(theta), float(eta), int(precision)
-        prm.tensor_cores = int(bool(tensor_cores))
+        prm.tensor_cores = int(tensor_cores)
         self.ctx = create(prm, device)
         self.N = int(np.asarray(xyz).shape[0])
         self.device = device

@@ -210,7 +210,7 @@ def test_mixed_form_meets_its_bar():
     op64.close()
     op32 = lmfmm.Operator(w.d, w.k, w.xyz, p=10, depth=4, theta=0.5,
                           precision=lmfmm.MIXED).build()
-    assert op32.stats()["m2l_kernel"] == 2      # default: tensor-core M2L
+    assert op32.stats()["m2l_kernel"] == 3      # default: persistent tensor-core M2L
     b = op32.matvec(Jt).cpu().numpy()
     op32.close()
     tg = rng.choice(w.N, 48, replace=False)
@@ -223,7 +223,8 @@ def test_mixed_form_meets_its_bar():
 def test_tensor_core_m2l(p):
     """Mixed form with the M2L product on the tcgen05 tensor cores (three-term
     TF32 split) against the FP64 form, next to the FP32 SIMT product: the
-    orders cover 1 to 4 row tiles of 128 (2P = 50 ... 512)."""
+    persistent kernel (p <= 13: 16 ... 208 table rows) and the streamed-operand
+    kernel (1 to 4 row tiles of 128: 2P = 50 ... 512)."""
     w = W.three_layer(n=4096, p=p, depth=3)
     Jt = torch.from_numpy(w.J).cuda()
     kw = dict(p=p, depth=3, theta=0.5)
@@ -231,14 +232,16 @@ def test_tensor_core_m2l(p):
     a = op.matvec(Jt).cpu().numpy()
     op.close()
     out = {}
-    for tc in (True, False):
+    expect = {0: 1, 1: 3 if p <= 13 else 2, 2: 2}
+    for tc in (0, 1, 2):
         op = lmfmm.Operator(w.d, w.k, w.xyz, precision=lmfmm.MIXED, tensor_cores=tc, **kw).build()
-        assert op.stats()["m2l_kernel"] == (2 if tc else 1)
+        assert op.stats()["m2l_kernel"] == expect[tc]
         out[tc] = op.matvec(Jt).cpu().numpy()
         op.close()
-    e_tc, e_simt = rel(out[True], a), rel(out[False], a)
-    print("p=%d tensor cores %.3e  SIMT %.3e" % (p, e_tc, e_simt))
-    assert e_tc < 5e-6 and e_tc < 3 * e_simt + 1e-7
+    e = {tc: rel(out[tc], a) for tc in out}
+    print("p=%d persistent %.3e  streamed %.3e  SIMT %.3e" % (p, e[1], e[2], e[0]))
+    for tc in (1, 2):
+        assert e[tc] < 5e-6 and e[tc] < 2 * e[0] + 1e-7
 
 
 def test_stats_before_first_matvec():
