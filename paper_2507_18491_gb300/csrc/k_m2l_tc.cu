@@ -371,27 +371,38 @@ __global__ void __launch_bounds__(NT) k_m2l_tc(int p, int MT, uint32_t tmem_cols
 // (f = -1 where a downward component or a mirrored box flips odd powers,
 // else 1; these are exact in any precision).  What is left per column is one
 // complex factor per input order m' (phase e^{i m' phi} and i^m') and one per
-// output order mu.  Roles (320 threads, one CTA per SM):
-//   warps 0-3  X producers: the work item's 64 columns, coefficients
-//              prefetched V2_D chunks ahead, split into TF32 hi/lo and written
-//              into a V2_SX-slot tensor-memory ring (A operand);
-//   warps 4-7  epilogue: accumulators -> a per-CTA scratch in global memory
-//              (L2-resident; tensor memory is free for the next item at once),
-//              then the output factors and float2 atomics into the local
-//              expansions;
-//   warp 8     one bulk copy per table chunk into an S_T-slot shared ring;
-//   warp 9     MMA issue: A_hi B_hi into one accumulator, A_hi B_lo + A_lo B_hi
-//              into a second (the tensor core truncates small addends against a
-//              large accumulator).
-// Every wait is bounded; a wait that gives up sets bit 4 of the status word
-// and its role stops.
+// output order mu.  Roles (576 threads, one CTA per SM -- the tensor memory
+// holds one CTA's accumulators, so latency is hidden by more warps per role):
+//   warps 0-7   X producers, two groups of four warps (one per tensor-memory
+//               lane quadrant) taking alternate K-chunks: the work item's 64
+//               columns, coefficients prefetched V2_D of the group's chunks
+//               ahead, split into TF32 hi/lo and written into a V2_SX-slot
+//               tensor-memory ring (A operand);
+//   warps 8-15  epilogue, two warps per lane quadrant taking alternate column
+//               slabs: accumulators -> a per-CTA scratch in global memory
+//               (L2-resident; tensor memory is free for the next item at
+//               once), then the output factors and float2 atomics into the
+//               local expansions;
+//   warp 16     one bulk copy per table chunk into an S_T-slot shared ring;
+//   warp 17     MMA issue: A_hi B_hi into one accumulator, A_hi B_lo + A_lo B_hi
+//               into a second (the tensor core truncates small addends against
+//               a large accumulator).
+// A chunk is V2_KS MMA K-steps of 8 real K, so that waits, fences and commits
+// are paid once per V2_KS steps; ring positions advance as counters (no
+// division in the loops).  Every wait is bounded; a wait that gives up sets
+// bit 4 of the status word and its role stops.
 namespace {
 
-constexpr int V2_SX = 6;           // X ring slots (tensor memory, 16 columns each)
+constexpr int V2_KS = 2;           // MMA K-steps (8 real K each) per ring chunk
+constexpr int V2_SX = 3;           // X ring slots (tensor memory, 16 * V2_KS columns each)
 constexpr int V2_ST_MAX = 16;      // table ring slots (shared memory)
-constexpr int V2_D = 8;            // coefficient chunks prefetched into registers
+constexpr int V2_PG = 2;           // producer groups (alternate chunks)
+constexpr int V2_D = 2;            // chunks of a group prefetched into registers
 constexpr int V2_NR_MAX = 208;     // table rows padded to 16: p <= 13
-constexpr int V2_THREADS = 320;
+constexpr int V2_PT = 128 * V2_PG; // producer threads
+constexpr int V2_ET = 256;         // epilogue threads
+constexpr int V2_WTMA = (V2_PT + V2_ET) / 32, V2_WMMA = V2_WTMA + 1;
+constexpr int V2_THREADS = (V2_WMMA + 1) * 32;
 constexpr uint32_t V2_SMEM_MAX = 227 * 1024;
 
 struct V2Col {
@@ -400,7 +411,7 @@ struct V2Col {
 };
 
 struct V2Plan {
-    uint32_t NR, nchunk, CB, ST, MO, g_bytes, meta_bytes, meta, tabs, bars, total;
+    uint32_t NR, nchunk, SB, CB, ST, MO, g_bytes, meta_bytes, meta, tabs, bars, total;
 };
 
 __host__ __device__ inline V2Plan v2_plan(int p)
@@ -408,8 +419,9 @@ __host__ __device__ inline V2Plan v2_plan(int p)
     const int P = (p + 1) * (p + 1);
     V2Plan s;
     s.NR = (uint32_t)((P + 15) & ~15);
-    s.nchunk = (uint32_t)((P + 3) / 4);
-    s.CB = s.NR * 64;                               // hi + lo image of a chunk: NR rows x 8 tf32 x 2
+    s.nchunk = (uint32_t)(((P + 3) / 4 + V2_KS - 1) / V2_KS);   // chunks of V2_KS K-steps
+    s.SB = s.NR * 64;                               // hi + lo image of a K-step: NR rows x 8 tf32 x 2
+    s.CB = V2_KS * s.SB;
     s.MO = 2 * p + 1;                               // orders -p..p
     s.g_bytes = BN * s.MO * 8;                      // one factor table: [64][2p+1] complex
     s.meta_bytes = 2 * s.g_bytes + BN * (uint32_t)sizeof(V2Col);
@@ -439,35 +451,38 @@ __device__ __forceinline__ cf mul_ipow(int k, cf v)
 //   input factors  G[pp][m'] = i^m' f_s^m' E[m'],
 //   output factors O[col][mh] = coef i^(1+kappa) (-i)^mu f_t^mu E[kappa - mu],
 //   mu = +-mh (sign of kappa), coef in {1/2, 1, -1/2};
-// and the column records
+// and the column records.  One warp per pair or column row, one lane per
+// order (2p+1 <= 32), so that the fill has no division and no divergence.
 __device__ __forceinline__ void v2_fill_meta(int p, int P, const M2LWork &w, const M2LPair *pairs,
                                              const cf *ephase, bool flip_in, bool flip_out, cf *G, cf *O,
-                                             V2Col *cols, int j, int nthr)
+                                             V2Col *cols, int tid, int nthr)
 {
     const int MO = 2 * p + 1, MW = 2 * p + 5;
     const int t = w.t, ncpp = (t == 1) ? 1 : 2, ncol = w.npair * ncpp;
-    for (int e = j; e < w.npair * MO; e += nthr) {
-        const int pp = e / MO, m = e % MO - p;
-        cf v = mul_ipow(m, ephase[(w.pair0 + pp) * MW + (p + 2) + m]);
-        if (flip_in && (m & 1)) v = -v;
-        G[pp * MO + p + m] = v;
+    const int lane = tid & 31, wi = tid >> 5, nw = nthr >> 5;
+    const int m = lane - p;                      // order of this lane
+    if (lane < MO) {
+        for (int pp = wi; pp < w.npair; pp += nw) {
+            cf v = mul_ipow(m, ephase[(w.pair0 + pp) * MW + (p + 2) + m]);
+            if (flip_in && (m & 1)) v = -v;
+            G[pp * MO + lane] = v;
+        }
+        for (int col = wi; col < ncol; col += nw) {
+            const int pp = ncpp == 1 ? col : col >> 1;
+            const ColSpec &cs = c_cols[t][ncpp == 1 ? 0 : col & 1];
+            const int mu = cs.kap < 0 ? -m : m;
+            float cf0 = (float)cs.coef;
+            if (cs.kap < 0 && (cs.kap & 1)) cf0 = -cf0;
+            if (flip_out && (mu & 1)) cf0 = -cf0;
+            const cf v = ephase[(w.pair0 + pp) * MW + (p + 2) + cs.kap - mu];
+            O[col * MO + lane] = cf0 * mul_ipow(1 + cs.kap - mu, v);
+        }
     }
-    for (int e = j; e < ncol * MO; e += nthr) {
-        const int col = e / MO, mh = e % MO - p;
-        const int pp = col / ncpp;
-        const ColSpec cs = c_cols[t][col % ncpp];
-        const int mu = cs.kap < 0 ? -mh : mh;
-        float cf0 = (float)cs.coef;
-        if (cs.kap < 0 && (cs.kap & 1)) cf0 = -cf0;
-        cf v = mul_ipow(1 + cs.kap - mu, ephase[(w.pair0 + pp) * MW + (p + 2) + cs.kap - mu]);
-        if (flip_out && (mu & 1)) cf0 = -cf0;
-        O[col * MO + p + mh] = cf0 * v;
-    }
-    for (int col = j; col < BN; col += nthr) {
+    for (int col = tid; col < BN; col += nthr) {
         V2Col q{};
         if (col < ncol) {
-            const int pp = col / ncpp;
-            const ColSpec cs = c_cols[t][col % ncpp];
+            const int pp = ncpp == 1 ? col : col >> 1;
+            const ColSpec &cs = c_cols[t][ncpp == 1 ? 0 : col & 1];
             const M2LPair pr = pairs[w.pair0 + pp];
             q.in_base = (pr.src * 3 + cs.vin) * (int64_t)P;
             q.out_base = (pr.tgt * 3 + cs.vout) * (int64_t)P;
@@ -516,14 +531,14 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
             tc::mbar_init(&xempty[s], 1);
         }
         tc::mbar_init(accfull, 1);
-        tc::mbar_init(accempty, 128);
+        tc::mbar_init(accempty, V2_ET);
         for (int i = 0; i < 2; ++i) {
-            tc::mbar_init(&metafull[i], 128);
-            tc::mbar_init(&metaempty[i], 128);
+            tc::mbar_init(&metafull[i], V2_PT);
+            tc::mbar_init(&metaempty[i], V2_ET);
         }
         tc::mbar_init(fin, 1);
-        tc::mbar_init(ydone, 128);
-        tc::mbar_init(yfree, 128);
+        tc::mbar_init(ydone, V2_ET);
+        tc::mbar_init(yfree, V2_ET);
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     for (int k = tid; k < P; k += V2_THREADS) {
@@ -539,55 +554,72 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
     const uint32_t tbase = *tslot;
     bool failed = false;
 
-    if (warp == 8) {
+    if (warp == V2_WTMA) {
         // ------------------------------------------------ table chunks
         if (lane == 0) {
-            uint32_t g = 0;
+            uint32_t g = 0, ph = 0;   // chunks issued; parity of the current pass over the ring
+            int s = 0;
             for (int64_t it = blockIdx.x; it < nwork && !failed; it += gridDim.x) {
                 const M2LWork w = work[it];
                 const int64_t ti = geoms[w.geom].tab_index * NTAB + w.t;
                 const unsigned char *src = (const unsigned char *)timg + (size_t)ti * nchunk * sp.CB;
-                for (int c = 0; c < nchunk; ++c, ++g) {
-                    const int s = g % ST;
-                    if (g >= (uint32_t)ST && !tc::mbar_wait(&tempty[s], ((g / ST) - 1) & 1, WAIT_POLLS)) {
+                for (int c = 0; c < nchunk; ++c) {
+                    if (g >= (uint32_t)ST && !tc::mbar_wait(&tempty[s], ph ^ 1, WAIT_POLLS)) {
                         failed = true;
                         break;
                     }
                     tc::mbar_expect_tx(&tfull[s], sp.CB);
                     tc::bulk_g2s(smraw + s * sp.CB, src + (size_t)c * sp.CB, sp.CB, &tfull[s]);
+                    ++g;
+                    if (++s == ST) {
+                        s = 0;
+                        ph ^= 1;
+                    }
                 }
             }
             // copies still in flight land before the CTA leaves
             for (uint32_t q = g > (uint32_t)ST ? g - ST : 0; q < g; ++q)
                 tc::mbar_wait(&tfull[q % ST], (q / ST) & 1, WAIT_POLLS);
         }
-    } else if (warp == 9) {
+    } else if (warp == V2_WMMA) {
         // ------------------------------------------------ MMA issue
         if (lane == 0) {
             const uint32_t idesc = tc::idesc_tf32(128, NR, false);
-            uint32_t g = 0, li = 0;
+            const uint32_t ring0 = tc::smem_u32(smraw);
+            uint32_t li = 0, tph = 0, xph = 0;
+            int st = 0, sx = 0;
             for (int64_t it = blockIdx.x; it < nwork && !failed; it += gridDim.x, ++li) {
                 if (li >= 1 && !tc::mbar_wait(accempty, (li - 1) & 1, WAIT_POLLS)) {
                     failed = true;
                     break;
                 }
                 tc::fence_after();
-                for (int c = 0; c < nchunk; ++c, ++g) {
-                    const int st = g % ST, sx = g % V2_SX;
-                    if (!tc::mbar_wait(&tfull[st], (g / ST) & 1, WAIT_POLLS) ||
-                        !tc::mbar_wait(&xfull[sx], (g / V2_SX) & 1, WAIT_POLLS)) {
+                for (int c = 0; c < nchunk; ++c) {
+                    if (!tc::mbar_wait(&tfull[st], tph, WAIT_POLLS) || !tc::mbar_wait(&xfull[sx], xph, WAIT_POLLS)) {
                         failed = true;
                         break;
                     }
                     tc::fence_after();
-                    const uint32_t ahi = tbase + XB + 16 * sx, alo = ahi + 8;
-                    const uint32_t bhi = tc::smem_u32(smraw + st * sp.CB), blo = bhi + NR * 32;
-                    const uint64_t dbh = tc::sdesc(bhi, 128, 256), dbl = tc::sdesc(blo, 128, 256);
-                    tc::mma_tf32_ta(tbase, ahi, dbh, idesc, c > 0 ? 1u : 0u);
-                    tc::mma_tf32_ta(tbase + NR, ahi, dbl, idesc, c > 0 ? 1u : 0u);
-                    tc::mma_tf32_ta(tbase + NR, alo, dbh, idesc, 1u);
+#pragma unroll
+                    for (int u = 0; u < V2_KS; ++u) {
+                        const uint32_t ahi = tbase + XB + 16 * (V2_KS * sx + u), alo = ahi + 8;
+                        const uint32_t bhi = ring0 + st * sp.CB + u * sp.SB, blo = bhi + NR * 32;
+                        const uint64_t dbh = tc::sdesc(bhi, 128, 256), dbl = tc::sdesc(blo, 128, 256);
+                        const uint32_t acc = (c > 0 || u > 0) ? 1u : 0u;
+                        tc::mma_tf32_ta(tbase, ahi, dbh, idesc, acc);
+                        tc::mma_tf32_ta(tbase + NR, ahi, dbl, idesc, acc);
+                        tc::mma_tf32_ta(tbase + NR, alo, dbh, idesc, 1u);
+                    }
                     tc::commit(&tempty[st]);
                     tc::commit(&xempty[sx]);
+                    if (++st == ST) {
+                        st = 0;
+                        tph ^= 1;
+                    }
+                    if (++sx == V2_SX) {
+                        sx = 0;
+                        xph ^= 1;
+                    }
                 }
                 if (failed) break;
                 tc::commit(accfull);
@@ -595,12 +627,18 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
             tc::commit(fin);   // every MMA issued above has completed once fin flips
             tc::mbar_wait(fin, 0, WAIT_POLLS);
         }
-    } else if (warp < 4) {
+    } else if (warp < V2_PT / 32) {
         // ------------------------------------------------ X producers
-        const int j = tid, cc = j >> 1, b = j & 1;
-        const uint32_t lane_base = tbase + ((uint32_t)(32 * warp) << 16);
-        uint32_t g = 0, li = 0;
-        for (int64_t it = blockIdx.x; it < nwork && !failed; it += gridDim.x, ++li) {
+        const int pg = warp / 4;                       // group: chunks g with g % V2_PG == pg
+        const int j = tid - pg * 128, cc = j >> 1, b = j & 1;
+        const uint32_t lane_base = tbase + ((uint32_t)(32 * (warp & 3)) << 16);
+        uint32_t g0 = 0, li = 0;                       // g0: chunks of this CTA before the item
+        // ring slot of this group's next chunk (global chunks pg, pg + V2_PG, ...),
+        // the parity of its pass and whether the ring has been gone round once
+        int xs = pg % V2_SX;
+        uint32_t xph = 0;
+        bool xwrapped = false;
+        for (int64_t it = blockIdx.x; it < nwork && !failed; it += gridDim.x, ++li, g0 += nchunk) {
             const int slot = li & 1;
             cf *G = meta_G(slot);
             V2Col *cols = meta_cols(slot);
@@ -610,7 +648,7 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
             const bool flip_out = (c.s < 0) != (c.has_tgt_refl != 0);
             bool ok = li < 2 || tc::mbar_wait(&metaempty[slot], ((li >> 1) - 1) & 1, WAIT_POLLS);
             if (ok) {
-                v2_fill_meta(p, P, w, pairs, ephase, flip_in, flip_out, G, meta_O(slot), cols, j, 128);
+                v2_fill_meta(p, P, w, pairs, ephase, flip_in, flip_out, G, meta_O(slot), cols, tid, V2_PT);
                 tc::mbar_arrive(&metafull[slot]);
                 ok = tc::mbar_wait(&metafull[slot], (li >> 1) & 1, WAIT_POLLS);
             }
@@ -625,63 +663,81 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
             const bool neg = q.kap < 0;
             const cf *gr = G + q.pp * MO + p;
             const cf *src = me + q.in_base;
-            float2 pre[V2_D][4];
-            // input (n', m') reads the expansion at (n', +-m'): index k or k - 2m'
-            auto fetch = [&](int ch, float2(&v)[4]) {
+            // this group's chunks of the item: c = cfirst, cfirst + V2_PG, ...
+            const int cfirst = (int)((pg + V2_PG - (int)(g0 % V2_PG)) % V2_PG);
+            const int nmine = cfirst < nchunk ? (nchunk - cfirst + V2_PG - 1) / V2_PG : 0;
+            constexpr int KC = 4 * V2_KS;          // complex inputs per chunk
+            float2 pre[V2_D][KC];
+            // input (n', m') reads the expansion at (n', +-m'): index k or k - 2m'.
+            // The load itself is unconditional (from a clamped address) so that
+            // it stays in flight until its use V2_D chunks later; the mask is
+            // applied there.
+            auto fetch = [&](int ch, float2(&v)[KC]) {
 #pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    const int k = 4 * ch + h;
-                    float2 x = make_float2(0.f, 0.f);
-                    if (valid && k < P) x = *(const float2 *)(src + (neg ? k - 2 * MM[k] : k));
-                    v[h] = x;
+                for (int h = 0; h < KC; ++h) {
+                    const int k = min(KC * ch + h, P - 1);
+                    const cf *a = valid ? src + (neg ? k - 2 * MM[k] : k) : me;
+                    v[h] = *(const float2 *)a;
                 }
             };
 #pragma unroll
             for (int u = 0; u < V2_D; ++u)
-                if (u < nchunk) fetch(u, pre[u]);
-            for (int c0 = 0; c0 < nchunk && !failed; c0 += V2_D) {
+                if (u < nmine) fetch(cfirst + u * V2_PG, pre[u]);
+            for (int q0 = 0; q0 < nmine && !failed; q0 += V2_D) {
 #pragma unroll
                 for (int u = 0; u < V2_D; ++u) {
-                    const int ch = c0 + u;
-                    if (ch >= nchunk) break;
-                    const int s = g % V2_SX;
-                    bool okw = g < (uint32_t)V2_SX || tc::mbar_wait(&xempty[s], ((g / V2_SX) - 1) & 1, WAIT_POLLS);
+                    const int qq = q0 + u;
+                    if (qq >= nmine) break;
+                    const int ch = cfirst + qq * V2_PG;
+                    bool okw = !xwrapped || tc::mbar_wait(&xempty[xs], xph ^ 1, WAIT_POLLS);
                     if (__any_sync(0xffffffffu, !okw)) {
                         failed = true;
                         break;
                     }
                     tc::fence_after();
-                    uint32_t hi[8], lo[8];
 #pragma unroll
-                    for (int h = 0; h < 4; ++h) {
-                        const int k = 4 * ch + h;
-                        float yr = 0.f, yi = 0.f;
-                        if (valid && k < P) {
-                            const int m = MM[k];
-                            const cf y = gr[neg ? -m : m] * cf{pre[u][h].x, pre[u][h].y};
-                            yr = y.x;
-                            yi = y.y;
+                    for (int sub = 0; sub < V2_KS; ++sub) {
+                        uint32_t hi[8], lo[8];
+#pragma unroll
+                        for (int h = 0; h < 4; ++h) {
+                            const int k = KC * ch + 4 * sub + h;
+                            float yr = 0.f, yi = 0.f;
+                            if (valid && k < P) {
+                                const int m = MM[k];
+                                const float2 x = pre[u][4 * sub + h];
+                                const cf y = gr[neg ? -m : m] * cf{x.x, x.y};
+                                yr = y.x;
+                                yi = y.y;
+                            }
+                            const float a0 = b ? yi : yr, a1 = b ? yr : -yi;
+                            const float h0 = tc::tf32_round(a0), h1 = tc::tf32_round(a1);
+                            hi[2 * h] = __float_as_uint(h0);
+                            hi[2 * h + 1] = __float_as_uint(h1);
+                            lo[2 * h] = __float_as_uint(tc::tf32_round(a0 - h0));
+                            lo[2 * h + 1] = __float_as_uint(tc::tf32_round(a1 - h1));
                         }
-                        const float a0 = b ? yi : yr, a1 = b ? yr : -yi;
-                        const float h0 = tc::tf32_round(a0), h1 = tc::tf32_round(a1);
-                        hi[2 * h] = __float_as_uint(h0);
-                        hi[2 * h + 1] = __float_as_uint(h1);
-                        lo[2 * h] = __float_as_uint(tc::tf32_round(a0 - h0));
-                        lo[2 * h + 1] = __float_as_uint(tc::tf32_round(a1 - h1));
+                        tc::tmem_st8(lane_base + XB + 16 * (V2_KS * xs + sub), hi);
+                        tc::tmem_st8(lane_base + XB + 16 * (V2_KS * xs + sub) + 8, lo);
                     }
-                    tc::tmem_st8(lane_base + XB + 16 * s, hi);
-                    tc::tmem_st8(lane_base + XB + 16 * s + 8, lo);
                     tc::tmem_st_wait();
                     tc::fence_before();
-                    tc::mbar_arrive(&xfull[s]);
-                    ++g;
-                    if (ch + V2_D < nchunk) fetch(ch + V2_D, pre[u]);
+                    tc::mbar_arrive(&xfull[xs]);
+                    // the group's next chunk is V2_PG ring slots further on
+                    xs += V2_PG;
+                    if (xs >= V2_SX) {
+                        xs -= V2_SX;
+                        xph ^= 1;
+                        xwrapped = true;
+                    }
+                    if (qq + V2_D < nmine) fetch(cfirst + (qq + V2_D) * V2_PG, pre[u]);
                 }
             }
         }
-    } else {
+    } else if (warp < V2_WTMA) {
         // ------------------------------------------------ epilogue
-        const int e = tid - 128, q4 = warp & 3;
+        const int ea = tid - V2_PT;                   // 0 .. V2_ET-1
+        const int q4 = warp & 3, half = ea / 128;     // lane quadrant, slab parity
+        const int e = 32 * q4 + lane;                 // real column = tensor-memory lane
         const uint32_t lane_base = tbase + ((uint32_t)(32 * q4) << 16);
         uint32_t li = 0;
         for (int64_t it = blockIdx.x; it < nwork && !failed; it += gridDim.x, ++li) {
@@ -693,7 +749,7 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
                 break;
             }
             tc::fence_after();
-            for (int c0 = 0; c0 < NR; c0 += 16) {   // NR is a multiple of 16
+            for (int c0 = 16 * half; c0 < NR; c0 += 32) {   // NR is a multiple of 16
                 uint32_t va[16], vb[16];
                 tc::tmem_ld16(lane_base + c0, va);
                 tc::tmem_ld16(lane_base + NR + c0, vb);
@@ -715,22 +771,37 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
             const int ncol = w.npair * ((w.t == 1) ? 1 : 2);
             const cf *O = meta_O(slot);
             const V2Col *cols = meta_cols(slot);
-            int cc = 0, r = e;
+            // outputs (column cc, row r) strided by V2_ET over the item; a batch
+            // of unconditional scratch reads is issued before its atomics
+            constexpr int EB = 8;
+            int cc = 0, r = ea;
             while (r >= P) {
                 r -= P;
                 ++cc;
             }
             while (cc < ncol) {
-                const V2Col &cq = cols[cc];
-                const float2 y = *(const float2 *)(Y + (size_t)r * 128 + 2 * cc);
-                const int mh = MM[r];
-                const cf yy = O[cc * MO + p + mh] * cf{y.x, y.y};
-                // output (nu, mu) with mu = +-mh: index r or r - 2 mh
-                atomicAdd((float2 *)(le + cq.out_base + (cq.kap < 0 ? r - 2 * mh : r)), make_float2(yy.x, yy.y));
-                r += 128;
-                while (r >= P) {
-                    r -= P;
-                    ++cc;
+                int bc[EB], br[EB];
+                float2 y[EB];
+#pragma unroll
+                for (int u = 0; u < EB; ++u) {
+                    bc[u] = cc;
+                    br[u] = r;
+                    y[u] = *(const float2 *)(Y + (size_t)r * 128 + 2 * min(cc, BN - 1));   // masked at use
+                    r += V2_ET;
+                    while (r >= P) {
+                        r -= P;
+                        ++cc;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < EB; ++u) {
+                    if (bc[u] >= ncol) break;
+                    const V2Col &cq = cols[bc[u]];
+                    const int mh = MM[br[u]];
+                    const cf yy = O[bc[u] * MO + p + mh] * cf{y[u].x, y[u].y};
+                    // output (nu, mu) with mu = +-mh: index r or r - 2 mh
+                    atomicAdd((float2 *)(le + cq.out_base + (cq.kap < 0 ? br[u] - 2 * mh : br[u])),
+                              make_float2(yy.x, yy.y));
                 }
             }
             tc::mbar_arrive(yfree);
@@ -743,9 +814,10 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
     if (warp == 0) tc::tmem_dealloc(tbase, 512);
 }
 
-// table image of the persistent kernel: per (geometry, table) nchunk chunks,
-// each the TF32 hi plane then the lo plane of NR rows x 8 real K in the
-// canonical K-major layout, from the FP64 table with the level scaling
+// table image of the persistent kernel: per (geometry, table) nchunk * V2_KS
+// K-steps (zero beyond P), each the TF32 hi plane then the lo plane of NR
+// rows x 8 real K in the canonical K-major layout, from the FP64 table with
+// the level scaling
 // s_t^nu s_s^n' and the degree factors (-i)^nu f_t^nu, i^n' f_s^n' applied
 // before the split
 __global__ void k_tile_tables(int p, int64_t g0, int64_t ng, const GeomDev *geoms, const CompDev *comps,
@@ -757,7 +829,8 @@ __global__ void k_tile_tables(int p, int64_t g0, int64_t ng, const GeomDev *geom
     const int64_t gi = g0 + blockIdx.y;
     const int t = blockIdx.z;
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (int)sp.nchunk * NR * 8 || gi >= g0 + ng) return;
+    const int nsub = (int)sp.nchunk * V2_KS;
+    if (e >= nsub * NR * 8 || gi >= g0 + ng) return;
     const int c = e / (NR * 8), rem = e % (NR * 8), r = rem >> 3, kk = rem & 7;
     const int k = 4 * c + (kk >> 1);
     const GeomDev &g = geoms[gi];
@@ -779,7 +852,7 @@ __global__ void k_tile_tables(int p, int64_t g0, int64_t ng, const GeomDev *geom
     }
     const float hi = tc::tf32_round((float)v);
     const float lo = tc::tf32_round((float)(v - (double)hi));
-    const size_t base = ((size_t)(g.tab_index * NTAB + t) * sp.nchunk + c) * (size_t)(NR * 16);
+    const size_t base = ((size_t)(g.tab_index * NTAB + t) * nsub + c) * (size_t)(NR * 16);
     const int off = ((r >> 3) * 256 + (kk >> 2) * 128 + (r & 7) * 16 + (kk & 3) * 4) >> 2;
     img[base + off] = hi;
     img[base + NR * 8 + off] = lo;
@@ -833,7 +906,7 @@ void launch_tile_tables(int p, int64_t g0, int64_t ng, const GeomDev *geoms, con
 {
     if (ng <= 0) return;
     const V2Plan sp = v2_plan(p);
-    dim3 grid((sp.nchunk * sp.NR * 8 + 255) / 256, (unsigned)ng, NTAB);
+    dim3 grid((sp.nchunk * V2_KS * sp.NR * 8 + 255) / 256, (unsigned)ng, NTAB);
     k_tile_tables<<<grid, 256, 0, st>>>(p, g0, ng, geoms, comps, tab64, img);
 }
 
