@@ -411,7 +411,7 @@ struct V2Col {
 };
 
 struct V2Plan {
-    uint32_t NR, nchunk, SB, CB, ST, MO, g_bytes, meta_bytes, meta, tabs, bars, total;
+    uint32_t NR, nchunk, SB, CB, ST, MO, g_bytes, meta_bytes, meta, tabs, mm_n, bars, total;
 };
 
 __host__ __device__ inline V2Plan v2_plan(int p)
@@ -425,12 +425,13 @@ __host__ __device__ inline V2Plan v2_plan(int p)
     s.MO = 2 * p + 1;                               // orders -p..p
     s.g_bytes = BN * s.MO * 8;                      // one factor table: [64][2p+1] complex
     s.meta_bytes = 2 * s.g_bytes + BN * (uint32_t)sizeof(V2Col);
-    const uint32_t fixed = 2 * s.meta_bytes + 4 * P + 16 + (2 * V2_ST_MAX + 2 * V2_SX + 12) * 8 + 16;
+    s.mm_n = 4 * V2_KS * s.nchunk;                  // order table, whole chunks (>= P)
+    const uint32_t fixed = 2 * s.meta_bytes + 2 * s.mm_n + 32 + (2 * V2_ST_MAX + 2 * V2_SX + 12) * 8 + 16;
     uint32_t st = (V2_SMEM_MAX - fixed) / s.CB;
     s.ST = st > V2_ST_MAX ? V2_ST_MAX : st;
     s.meta = s.ST * s.CB;
-    s.tabs = s.meta + 2 * s.meta_bytes;
-    s.bars = (s.tabs + 4 * P + 15) & ~15u;
+    s.tabs = (s.meta + 2 * s.meta_bytes + 15) & ~15u;
+    s.bars = (s.tabs + 2 * s.mm_n + 15) & ~15u;
     s.total = s.bars + (2 * V2_ST_MAX + 2 * V2_SX + 12) * 8 + 16;
     return s;
 }
@@ -461,21 +462,42 @@ __device__ __forceinline__ void v2_fill_meta(int p, int P, const M2LWork &w, con
     const int t = w.t, ncpp = (t == 1) ? 1 : 2, ncol = w.npair * ncpp;
     const int lane = tid & 31, wi = tid >> 5, nw = nthr >> 5;
     const int m = lane - p;                      // order of this lane
+    // rows per warp: at most RB (npair, ncol <= 64 over nw >= 8 warps); all
+    // loads of a warp are issued before the first use
+    constexpr int RB = 8;
     if (lane < MO) {
-        for (int pp = wi; pp < w.npair; pp += nw) {
-            cf v = mul_ipow(m, ephase[(w.pair0 + pp) * MW + (p + 2) + m]);
-            if (flip_in && (m & 1)) v = -v;
-            G[pp * MO + lane] = v;
+        cf v[RB];
+#pragma unroll
+        for (int i = 0; i < RB; ++i) {
+            const int pp = min(wi + i * nw, w.npair - 1);
+            v[i] = ephase[(w.pair0 + pp) * MW + (p + 2) + m];
         }
-        for (int col = wi; col < ncol; col += nw) {
+#pragma unroll
+        for (int i = 0; i < RB; ++i) {
+            const int pp = wi + i * nw;
+            if (pp >= w.npair) break;
+            cf x = mul_ipow(m, v[i]);
+            if (flip_in && (m & 1)) x = -x;
+            G[pp * MO + lane] = x;
+        }
+#pragma unroll
+        for (int i = 0; i < RB; ++i) {
+            const int col = min(wi + i * nw, ncol - 1);
             const int pp = ncpp == 1 ? col : col >> 1;
+            const ColSpec &cs = c_cols[t][ncpp == 1 ? 0 : col & 1];
+            const int mu = cs.kap < 0 ? -m : m;
+            v[i] = ephase[(w.pair0 + pp) * MW + (p + 2) + cs.kap - mu];
+        }
+#pragma unroll
+        for (int i = 0; i < RB; ++i) {
+            const int col = wi + i * nw;
+            if (col >= ncol) break;
             const ColSpec &cs = c_cols[t][ncpp == 1 ? 0 : col & 1];
             const int mu = cs.kap < 0 ? -m : m;
             float cf0 = (float)cs.coef;
             if (cs.kap < 0 && (cs.kap & 1)) cf0 = -cf0;
             if (flip_out && (mu & 1)) cf0 = -cf0;
-            const cf v = ephase[(w.pair0 + pp) * MW + (p + 2) + cs.kap - mu];
-            O[col * MO + lane] = cf0 * mul_ipow(1 + cs.kap - mu, v);
+            O[col * MO + lane] = cf0 * mul_ipow(1 + cs.kap - mu, v[i]);
         }
     }
     for (int col = tid; col < BN; col += nthr) {
@@ -504,7 +526,7 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
     const int P = (p + 1) * (p + 1);
     const V2Plan sp = v2_plan(p);
     const int NR = (int)sp.NR, nchunk = (int)sp.nchunk, ST = (int)sp.ST, MO = (int)sp.MO;
-    short *DEG = (short *)(smraw + sp.tabs), *MM = DEG + P;   // degree n and order m of index k
+    short *MM = (short *)(smraw + sp.tabs);   // order m of index k = n^2 + n + m (0 beyond P)
     uint64_t *bars = (uint64_t *)(smraw + sp.bars);
     uint64_t *tfull = bars, *tempty = bars + V2_ST_MAX, *xfull = bars + 2 * V2_ST_MAX,
              *xempty = xfull + V2_SX;
@@ -541,12 +563,11 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
         tc::mbar_init(yfree, V2_ET);
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
-    for (int k = tid; k < P; k += V2_THREADS) {
+    for (int k = tid; k < (int)sp.mm_n; k += V2_THREADS) {
         int n = (int)sqrtf((float)k + 0.5f);
         while ((n + 1) * (n + 1) <= k) ++n;
         while (n * n > k) --n;
-        DEG[k] = (short)n;
-        MM[k] = (short)(k - n * n - n);
+        MM[k] = k < P ? (short)(k - n * n - n) : (short)0;
     }
     tc::fence_before();
     __syncthreads();
@@ -585,7 +606,12 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
         // ------------------------------------------------ MMA issue
         if (lane == 0) {
             const uint32_t idesc = tc::idesc_tf32(128, NR, false);
-            const uint32_t ring0 = tc::smem_u32(smraw);
+            // descriptor of ring slot 0; the address field counts 16-byte units,
+            // so slot, K-step and lo-plane offsets add to it directly
+            const uint64_t dring0 = tc::sdesc(tc::smem_u32(smraw), 128, 256);
+            const uint64_t d_cb = sp.CB >> 4, d_sb = sp.SB >> 4, d_lo = (uint32_t)(NR * 32) >> 4;
+            uint64_t dslot = dring0;                       // descriptor of table slot st
+            uint32_t aslot = tbase + XB;                   // tensor-memory address of X slot sx
             uint32_t li = 0, tph = 0, xph = 0;
             int st = 0, sx = 0;
             for (int64_t it = blockIdx.x; it < nwork && !failed; it += gridDim.x, ++li) {
@@ -602,9 +628,8 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
                     tc::fence_after();
 #pragma unroll
                     for (int u = 0; u < V2_KS; ++u) {
-                        const uint32_t ahi = tbase + XB + 16 * (V2_KS * sx + u), alo = ahi + 8;
-                        const uint32_t bhi = ring0 + st * sp.CB + u * sp.SB, blo = bhi + NR * 32;
-                        const uint64_t dbh = tc::sdesc(bhi, 128, 256), dbl = tc::sdesc(blo, 128, 256);
+                        const uint32_t ahi = aslot + 16 * u, alo = ahi + 8;
+                        const uint64_t dbh = dslot + u * d_sb, dbl = dbh + d_lo;
                         const uint32_t acc = (c > 0 || u > 0) ? 1u : 0u;
                         tc::mma_tf32_ta(tbase, ahi, dbh, idesc, acc);
                         tc::mma_tf32_ta(tbase + NR, ahi, dbl, idesc, acc);
@@ -612,13 +637,17 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
                     }
                     tc::commit(&tempty[st]);
                     tc::commit(&xempty[sx]);
+                    dslot += d_cb;
+                    aslot += 16 * V2_KS;
                     if (++st == ST) {
                         st = 0;
                         tph ^= 1;
+                        dslot = dring0;
                     }
                     if (++sx == V2_SX) {
                         sx = 0;
                         xph ^= 1;
+                        aslot = tbase + XB;
                     }
                 }
                 if (failed) break;
@@ -672,11 +701,20 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
             // The load itself is unconditional (from a clamped address) so that
             // it stays in flight until its use V2_D chunks later; the mask is
             // applied there.
+            static_assert(KC == 8, "one 16-byte load of the order table per chunk");
+            auto orders = [&](int ch, int(&mo)[KC]) {
+                const uint4 q4 = *(const uint4 *)(MM + KC * ch);
+                const uint32_t wv[4] = {q4.x, q4.y, q4.z, q4.w};
+#pragma unroll
+                for (int h = 0; h < KC; ++h) mo[h] = (int)(short)(wv[h >> 1] >> (16 * (h & 1)));
+            };
             auto fetch = [&](int ch, float2(&v)[KC]) {
+                int mo[KC];
+                orders(ch, mo);
 #pragma unroll
                 for (int h = 0; h < KC; ++h) {
                     const int k = min(KC * ch + h, P - 1);
-                    const cf *a = valid ? src + (neg ? k - 2 * MM[k] : k) : me;
+                    const cf *a = valid ? src + (neg ? k - 2 * mo[h] : k) : me;
                     v[h] = *(const float2 *)a;
                 }
             };
@@ -695,6 +733,8 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
                         break;
                     }
                     tc::fence_after();
+                    int mo[KC];
+                    orders(ch, mo);
 #pragma unroll
                     for (int sub = 0; sub < V2_KS; ++sub) {
                         uint32_t hi[8], lo[8];
@@ -703,7 +743,7 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
                             const int k = KC * ch + 4 * sub + h;
                             float yr = 0.f, yi = 0.f;
                             if (valid && k < P) {
-                                const int m = MM[k];
+                                const int m = mo[4 * sub + h];
                                 const float2 x = pre[u][4 * sub + h];
                                 const cf y = gr[neg ? -m : m] * cf{x.x, x.y};
                                 yr = y.x;
@@ -773,7 +813,7 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
             const V2Col *cols = meta_cols(slot);
             // outputs (column cc, row r) strided by V2_ET over the item; a batch
             // of unconditional scratch reads is issued before its atomics
-            constexpr int EB = 8;
+            constexpr int EB = 16;
             int cc = 0, r = ea;
             while (r >= P) {
                 r -= P;
