@@ -34,6 +34,18 @@ sys.path.insert(0, ROOT)
 SM_COUNT, SM_MHZ = 152, 2070.0
 FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * SM_MHZ * 1e6 / 1e12
 FP64_PEAK_TFLOPS = SM_COUNT * 2 * 2 * SM_MHZ * 1e6 / 1e12
+# dense TF32 tensor peak: the measured bf16 burst peak times the nominal
+# TF32 / bf16 ratio (1.1 / 2.25 PFLOP/s); fallback 1.9 PFLOP/s bf16
+TF32_PER_BF16 = 1.1 / 2.25
+
+
+def tf32_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            bf16 = float(json.load(f)["bf16_tflops"])
+        return bf16 * TF32_PER_BF16, "of measured: bf16 burst %.1f TFLOP/s x nominal tf32/bf16 1.1/2.25" % bf16
+    except (OSError, KeyError, ValueError):
+        return 1900.0 * TF32_PER_BF16, "of fallback: bf16 1900 TFLOP/s x nominal tf32/bf16 1.1/2.25"
 
 
 def workload(name, seed_shift=0):
@@ -255,8 +267,12 @@ def main():
     m2l_s = float(np.mean(m2l_ms)) * 1e-3
     achieved = flops / m2l_s / 1e12
     launches_per_step = 6 + 2 * st["depth"]
+    kern = {0: "k_m2l<double>", 1: "k_m2l<float>", 2: "k_m2l_tc", 3: "k_m2l_tc2"}[st["m2l_kernel"]]
+    bound = "tensor" if st["m2l_kernel"] >= 2 else "alu"
     if prec == lmfmm.FP64:
         peak, peak_src = FP64_PEAK_TFLOPS, "derived FP64 ALU: 152 SM x 2 FMA/clk x 2 x 2070 MHz"
+    elif bound == "tensor":
+        peak, peak_src = tf32_peak()
     else:
         peak, peak_src = FP32_PEAK_TFLOPS, "derived FP32 ALU: 152 SM x 128 FMA/clk x 2 x 2070 MHz"
     line = {
@@ -275,9 +291,11 @@ def main():
         "e2e": {"value": ws * w.N / (e2e_ms * 1e-3) / 1e6, "unit": "Mtargets/s",
                 "h2d_bytes_per_step": int(w.N * 3 * 16), "d2h_bytes_per_step": int(w.N * 3 * 16)},
         "gpu_launches": launches_per_step * args.steps,
-        "roofline": {"kernel": "k_m2l", "bound": "alu", "achieved": achieved,
+        "roofline": {"kernel": kern, "bound": bound, "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                     "peak_source": peak_src, "flops_per_launch": flops},
+                     "peak_source": peak_src, "flops_per_launch": flops,
+                     "flops_definition": "algorithmic: 8 P^2 real flops per M2L column (complex P x P "
+                                         "product); the tensor path executes 3 TF32 terms of each"},
     }
     if rank == 0 and not args.no_cpu:
         line["config"]["rel_err_vs_oracle"] = accuracy(op, w)
