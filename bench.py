@@ -268,6 +268,10 @@ def main():
     achieved = flops / m2l_s / 1e12
     launches_per_step = 6 + 2 * st["depth"]
     kern = {0: "k_m2l<double>", 1: "k_m2l<float>", 2: "k_m2l_tc", 3: "k_m2l_tc2"}[st["m2l_kernel"]]
+    # DRAM bytes per launch of k_m2l_tc2: the table image times the read+write / image
+    # ratio of an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum = 5.23 GB for a
+    # 4.92 GB image, three-layer N = 8192, p = 12); other kernels: not captured
+    traffic = st["bytes_tables"] * (5.229 / 4.918) if st["m2l_kernel"] == 3 else None
     bound = "tensor" if st["m2l_kernel"] >= 2 else "alu"
     if prec == lmfmm.FP64:
         peak, peak_src = FP64_PEAK_TFLOPS, "derived FP64 ALU: 152 SM x 2 FMA/clk x 2 x 2070 MHz"
@@ -292,7 +296,7 @@ def main():
                 "h2d_bytes_per_step": int(w.N * 3 * 16), "d2h_bytes_per_step": int(w.N * 3 * 16)},
         "gpu_launches": launches_per_step * args.steps,
         "roofline": {"kernel": kern, "bound": bound, "achieved": achieved,
-                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_source": peak_src, "flops_per_launch": flops,
                      "flops_definition": "algorithmic: 8 P^2 real flops per M2L column (complex P x P "
                                          "product); the tensor path executes 3 TF32 terms of each"},
