@@ -39,7 +39,9 @@ struct DevState {
     GemmWork *gwork = nullptr;
     std::vector<int64_t> gwork_off;  // per child level: [off[l], off[l+1])
     NearPair *near = nullptr;
-    cd *s2t = nullptr;
+    cd *s2t = nullptr;               // near field: 8 combined coefficients per point pair
+    S2TWork *s2twork = nullptr;      // near-field work items
+    int64_t n_s2twork = 0;
     int *flag = nullptr;
     int *mvstatus = nullptr;         // matvec status word (bit 4: tensor-core wait gave up)
     int m2l_kernel = 0;              // 0 FP64 SIMT, 1 FP32 SIMT, 2 tcgen05 streamed, 3 tcgen05 persistent
@@ -375,7 +377,7 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
                                   (double)ctx->m2l.size() * (2 * p + 5) * 8.0
                             : 0.0) +
                   (double)nbox * 6 * P * 16.0 + (double)ctx->tgroups.size() * 2 * P * P * 16.0 +
-                  (double)ctx->n_near_pp * 5 * 16.0 + (double)N * 200.0;
+                  (double)ctx->n_near_pp * 13 * 16.0 + (double)N * 200.0;
     size_t fr = 0, tot = 0;
     CK(cudaMemGetInfo(&fr, &tot));
     if (need > 0.85 * (double)fr) {
@@ -583,11 +585,29 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
     }
     // near field
     TRY(dupload(ctx, &d->near, ctx->near));
-    TRY(dalloc(ctx, &d->s2t, (size_t)ctx->n_near_pp * 5));
-    launch_s2t_pre((int64_t)ctx->near.size(), d->near, d->boxes, d->xyz, ctx->med, d->comps, a,
-                   0.5 * a, d->s2t, d->flag, st);
-    CK(cudaGetLastError());
-    CK(cudaStreamSynchronize(st));
+    {
+        // five Sommerfeld integrals per point pair, then the 8 combined coefficients
+        cd *s2t5 = nullptr;
+        TRY(dalloc(ctx, &s2t5, (size_t)ctx->n_near_pp * 5));
+        launch_s2t_pre((int64_t)ctx->near.size(), d->near, d->boxes, d->xyz, ctx->med, d->comps, a,
+                       0.5 * a, s2t5, d->flag, st);
+        CK(cudaGetLastError());
+        TRY(dalloc(ctx, &d->s2t, (size_t)ctx->n_near_pp * 8));
+        launch_s2t_combine((int64_t)ctx->near.size(), d->near, d->boxes, d->xyz, s2t5, d->s2t, st);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(st));
+        dfree(ctx, s2t5);
+        std::vector<S2TWork> sw;
+        for (size_t i = 0; i < ctx->near.size(); ++i) {
+            const NearPair &q = ctx->near[i];
+            const Box &bs = ctx->boxes[q.src], &bt = ctx->boxes[q.tgt];
+            for (int64_t t0 = 0; t0 < bt.p1 - bt.p0; t0 += S2T_BLK)
+                for (int64_t s0 = 0; s0 < bs.p1 - bs.p0; s0 += S2T_BLK)
+                    sw.push_back(S2TWork{(int64_t)i, (int)t0, (int)s0});
+        }
+        TRY(dupload(ctx, &d->s2twork, sw));
+        d->n_s2twork = (int64_t)sw.size();
+    }
     TRY(check_flag(ctx));
     ctx->built = true;
     auto t1 = std::chrono::steady_clock::now();
@@ -656,8 +676,7 @@ static lmfmm_status matvec_t(lmfmm_ctx *ctx, const lmfmm_c128 *J, lmfmm_c128 *Ph
     CK(cudaEventRecord(d->ev[4], st));
     launch_l2p<T>(p, d->nleaves, d->leaves, d->boxes, d->xyz, le, ctx->med, d->lscale, d->ph, st);
     CK(cudaEventRecord(d->ev[5], st));
-    launch_s2t_apply((int64_t)ctx->near.size(), d->near, d->boxes, d->xyz, d->s2t, d->qh, d->ph,
-                     st);
+    launch_s2t_apply8(d->n_s2twork, d->s2twork, d->near, d->boxes, d->s2t, d->qh, d->ph, st);
     CK(cudaEventRecord(d->ev[6], st));
     launch_scatter_out(N, d->perm, d->ph, (cd *)Phi, cj, st);
     CK(cudaEventRecord(d->ev[7], st));

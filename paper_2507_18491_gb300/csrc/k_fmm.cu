@@ -391,6 +391,95 @@ __global__ void k_s2t_apply(const NearPair *near, const BoxDev *boxes, const dou
     }
 }
 
+// The matvec's near field with the angular factors and constants of the
+// helical form folded in once at setup: for target i and source j of a near
+// pair, with e = e^{i phi} (phi the horizontal angle of r_j - r_i) and
+// c = 1/(4 pi),
+//   A += k0 a + k6 b + k2 c_,   B += k0 b + k7 a + k3 c_,   C += k1 c_ + k5 a + k4 b,
+//   k0 = i c I0 / 2,  k1 = i c I1,  k2 = -c e I2,  k3 = -c conj(e) I2,
+//   k4 = -c e I3 / 2,  k5 = -c conj(e) I3 / 2,  k6 = i c e^2 I4 / 2,  k7 = i c conj(e)^2 I4 / 2,
+// (a, b, c_) the helical charges; I0..I4 the five Sommerfeld integrals of
+// k_s2t_pre (same terms as k_s2t_apply).  Layout per near pair: [j][k0..k7][i],
+// consecutive targets contiguous, 8 coefficients per point pair.
+__global__ void k_s2t_combine(const NearPair *near, const BoxDev *boxes, const double *xyz,
+                              const cd *coef5, cd *coef8)
+{
+    NearPair np = near[blockIdx.x];
+    BoxDev B = boxes[np.src], C = boxes[np.tgt];
+    const int64_t nB = B.p1 - B.p0, nC = C.p1 - C.p0;
+    const cd *I5 = coef5 + np.coef0 * 5;
+    cd *K = coef8 + np.coef0 * 8;
+    const double f = 1.0 / (4.0 * LMF_PI);
+    for (int64_t e = threadIdx.x; e < nB * nC; e += blockDim.x) {
+        const int64_t ii = e / nB, jj = e % nB;
+        const int64_t ti = C.p0 + ii, sj = B.p0 + jj;
+        const double dx = xyz[3 * sj] - xyz[3 * ti], dy = xyz[3 * sj + 1] - xyz[3 * ti + 1];
+        const double rho = sqrt(dx * dx + dy * dy);
+        const cd e1 = rho > 0 ? cd{dx / rho, dy / rho} : cd{1.0, 0.0}, e2 = e1 * e1;
+        const cd *I = I5 + e * 5;
+        cd k[8];
+        k[0] = mkd(0.0, 0.5 * f) * I[0];
+        k[1] = mkd(0.0, f) * I[1];
+        k[2] = -f * (e1 * I[2]);
+        k[3] = -f * (conj(e1) * I[2]);
+        k[4] = (-0.5 * f) * (e1 * I[3]);
+        k[5] = (-0.5 * f) * (conj(e1) * I[3]);
+        k[6] = mkd(0.0, 0.5 * f) * (e2 * I[4]);
+        k[7] = mkd(0.0, 0.5 * f) * (conj(e2) * I[4]);
+        for (int u = 0; u < 8; ++u) K[(jj * 8 + u) * nC + ii] = k[u];
+    }
+}
+
+// Phi_h(i) += near-field terms of k_s2t_combine's coefficients.  One CTA per
+// work item: up to S2T_BLK targets (one per thread) of one near pair against
+// up to S2T_BLK of its sources, so that crowded box pairs spread over many
+// CTAs; charges are broadcast across the warp, coefficients coalesced over
+// targets.
+__global__ void k_s2t_apply8(const S2TWork *work, const NearPair *near, const BoxDev *boxes,
+                             const cd *coef8, const cd *qh, cd *ph)
+{
+    const S2TWork w = work[blockIdx.x];
+    const NearPair np = near[w.pair];
+    const BoxDev B = boxes[np.src], C = boxes[np.tgt];
+    const int64_t nC = C.p1 - C.p0;
+    const int64_t ii = w.t0 + threadIdx.x;
+    const int64_t j1 = min((int64_t)w.s0 + S2T_BLK, B.p1 - B.p0);
+    if (ii >= nC) return;
+    const cd *K = coef8 + np.coef0 * 8;
+    cd A = mkd(0.0), Bv = mkd(0.0), Cv = mkd(0.0);
+    for (int64_t jj = w.s0; jj < j1; ++jj) {
+        const cd *k = K + jj * 8 * nC + ii;
+        const int64_t sj = B.p0 + jj;
+        const cd a = qh[3 * sj], b = qh[3 * sj + 1], c = qh[3 * sj + 2];
+        const cd k0 = k[0], k1 = k[nC], k2 = k[2 * nC], k3 = k[3 * nC], k4 = k[4 * nC], k5 = k[5 * nC],
+                 k6 = k[6 * nC], k7 = k[7 * nC];
+        A += k0 * a + k6 * b + k2 * c;
+        Bv += k0 * b + k7 * a + k3 * c;
+        Cv += k1 * c + k5 * a + k4 * b;
+    }
+    const int64_t ti = C.p0 + ii;
+    atomicAdd(&ph[3 * ti].x, A.x);
+    atomicAdd(&ph[3 * ti].y, A.y);
+    atomicAdd(&ph[3 * ti + 1].x, Bv.x);
+    atomicAdd(&ph[3 * ti + 1].y, Bv.y);
+    atomicAdd(&ph[3 * ti + 2].x, Cv.x);
+    atomicAdd(&ph[3 * ti + 2].y, Cv.y);
+}
+
+void launch_s2t_combine(int64_t nnear, const NearPair *near, const BoxDev *boxes, const double *xyz,
+                        const cd *coef5, cd *coef8, cudaStream_t st)
+{
+    if (nnear <= 0) return;
+    k_s2t_combine<<<(unsigned)nnear, 128, 0, st>>>(near, boxes, xyz, coef5, coef8);
+}
+
+void launch_s2t_apply8(int64_t nwork, const S2TWork *work, const NearPair *near, const BoxDev *boxes,
+                       const cd *coef8, const cd *qh, cd *phih, cudaStream_t st)
+{
+    if (nwork <= 0) return;
+    k_s2t_apply8<<<(unsigned)nwork, S2T_BLK, 0, st>>>(work, near, boxes, coef8, qh, phih);
+}
+
 void launch_s2t_apply(int64_t nnear, const NearPair *near, const BoxDev *boxes,
                       const double *xyz, const cd *coef, const cd *qh, cd *phih,
                       cudaStream_t st)

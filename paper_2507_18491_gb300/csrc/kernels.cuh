@@ -119,6 +119,18 @@ void launch_scale_tables(int p, int64_t g0, int64_t ng, const GeomDev *geoms, co
 void launch_s2t_pre(int64_t nnear, const NearPair *near, const BoxDev *boxes, const double *xyz,
                     const MediumDev &M, const CompDev *comps, double a, double kp, cd *coef,
                     int *dflag, cudaStream_t st);
+// matvec near field: 8 combined coefficients per point pair ([j][8][i] per near pair)
+void launch_s2t_combine(int64_t nnear, const NearPair *near, const BoxDev *boxes, const double *xyz,
+                        const cd *coef5, cd *coef8, cudaStream_t st);
+// work item of the matvec near field: targets [t0, t0 + S2T_BLK) of near pair
+// `pair` against its sources [s0, s0 + S2T_BLK)
+constexpr int S2T_BLK = 64;
+struct S2TWork {
+    int64_t pair;
+    int t0, s0;
+};
+void launch_s2t_apply8(int64_t nwork, const S2TWork *work, const NearPair *near, const BoxDev *boxes,
+                       const cd *coef8, const cd *qh, cd *phih, cudaStream_t st);
 void launch_s2t_apply(int64_t nnear, const NearPair *near, const BoxDev *boxes,
                       const double *xyz, const cd *coef, const cd *qh, cd *phih,
                       cudaStream_t st);
