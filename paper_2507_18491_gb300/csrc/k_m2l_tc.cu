@@ -436,6 +436,19 @@ __host__ __device__ inline V2Plan v2_plan(int p)
     return s;
 }
 
+__device__ __forceinline__ cf lds_cf(uint32_t a)
+{
+    cf v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ uint4 lds_u4(uint32_t a)
+{
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
+    return v;
+}
+
 // i^k v, exact
 __device__ __forceinline__ cf mul_ipow(int k, cf v)
 {
@@ -531,7 +544,7 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
     uint64_t *tfull = bars, *tempty = bars + V2_ST_MAX, *xfull = bars + 2 * V2_ST_MAX,
              *xempty = xfull + V2_SX;
     uint64_t *accfull = xempty + V2_SX, *accempty = accfull + 1, *metafull = accfull + 2,
-             *metaempty = accfull + 4, *fin = accfull + 6, *ydone = accfull + 7, *yfree = accfull + 8;
+             *fin = accfull + 6, *ydone = accfull + 7, *yfree = accfull + 8;
     uint32_t *tslot = (uint32_t *)(accfull + 9);
     auto meta_G = [&](int slot) { return (cf *)(smraw + sp.meta + slot * sp.meta_bytes); };
     auto meta_O = [&](int slot) { return (cf *)(smraw + sp.meta + slot * sp.meta_bytes + sp.g_bytes); };
@@ -555,8 +568,7 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
         tc::mbar_init(accfull, 1);
         tc::mbar_init(accempty, V2_ET);
         for (int i = 0; i < 2; ++i) {
-            tc::mbar_init(&metafull[i], V2_PT);
-            tc::mbar_init(&metaempty[i], V2_ET);
+            tc::mbar_init(&metafull[i], V2_ET);
         }
         tc::mbar_init(fin, 1);
         tc::mbar_init(ydone, V2_ET);
@@ -672,15 +684,8 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
             cf *G = meta_G(slot);
             V2Col *cols = meta_cols(slot);
             const M2LWork w = work[it];
-            const CompDev c = comps[geoms[w.geom].comp];
-            const bool flip_in = (c.s < 0) != (c.has_src_refl != 0);
-            const bool flip_out = (c.s < 0) != (c.has_tgt_refl != 0);
-            bool ok = li < 2 || tc::mbar_wait(&metaempty[slot], ((li >> 1) - 1) & 1, WAIT_POLLS);
-            if (ok) {
-                v2_fill_meta(p, P, w, pairs, ephase, flip_in, flip_out, G, meta_O(slot), cols, tid, V2_PT);
-                tc::mbar_arrive(&metafull[slot]);
-                ok = tc::mbar_wait(&metafull[slot], (li >> 1) & 1, WAIT_POLLS);
-            }
+            // column data of the item, filled by the epilogue warps
+            const bool ok = tc::mbar_wait(&metafull[slot], (li >> 1) & 1, WAIT_POLLS);
             if (__any_sync(0xffffffffu, !ok)) {
                 failed = true;
                 break;
@@ -690,7 +695,7 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
             V2Col q{};
             if (valid) q = cols[cc];
             const bool neg = q.kap < 0;
-            const cf *gr = G + q.pp * MO + p;
+            const uint32_t gr = tc::smem_u32(G + q.pp * MO + p);   // input factors of the column
             const cf *src = me + q.in_base;
             // this group's chunks of the item: c = cfirst, cfirst + V2_PG, ...
             const int cfirst = (int)((pg + V2_PG - (int)(g0 % V2_PG)) % V2_PG);
@@ -702,8 +707,9 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
             // it stays in flight until its use V2_D chunks later; the mask is
             // applied there.
             static_assert(KC == 8, "one 16-byte load of the order table per chunk");
+            const uint32_t mm0 = tc::smem_u32(MM);
             auto orders = [&](int ch, int(&mo)[KC]) {
-                const uint4 q4 = *(const uint4 *)(MM + KC * ch);
+                const uint4 q4 = lds_u4(mm0 + 2 * KC * ch);
                 const uint32_t wv[4] = {q4.x, q4.y, q4.z, q4.w};
 #pragma unroll
                 for (int h = 0; h < KC; ++h) mo[h] = (int)(short)(wv[h >> 1] >> (16 * (h & 1)));
@@ -745,7 +751,7 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
                             if (valid && k < P) {
                                 const int m = mo[4 * sub + h];
                                 const float2 x = pre[u][4 * sub + h];
-                                const cf y = gr[neg ? -m : m] * cf{x.x, x.y};
+                                const cf y = lds_cf(gr + 8 * (neg ? -m : m)) * cf{x.x, x.y};
                                 yr = y.x;
                                 yi = y.y;
                             }
@@ -779,11 +785,22 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
         const int q4 = warp & 3, half = ea / 128;     // lane quadrant, slab parity
         const int e = 32 * q4 + lane;                 // real column = tensor-memory lane
         const uint32_t lane_base = tbase + ((uint32_t)(32 * q4) << 16);
+        // column data of item `it` into meta slot `slot`, then release it to the producers
+        auto fill = [&](int64_t it, int slot) {
+            const M2LWork w = work[it];
+            const CompDev c = comps[geoms[w.geom].comp];
+            const bool flip_in = (c.s < 0) != (c.has_src_refl != 0);
+            const bool flip_out = (c.s < 0) != (c.has_tgt_refl != 0);
+            v2_fill_meta(p, P, w, pairs, ephase, flip_in, flip_out, meta_G(slot), meta_O(slot), meta_cols(slot),
+                         ea, V2_ET);
+            tc::mbar_arrive(&metafull[slot]);
+        };
+        for (int i = 0; i < 2; ++i)
+            if (blockIdx.x + (int64_t)i * gridDim.x < nwork) fill(blockIdx.x + (int64_t)i * gridDim.x, i);
         uint32_t li = 0;
         for (int64_t it = blockIdx.x; it < nwork && !failed; it += gridDim.x, ++li) {
             const int slot = li & 1;
             bool ok = tc::mbar_wait(accfull, li & 1, WAIT_POLLS);
-            if (ok && li >= 1) ok = tc::mbar_wait(yfree, (li - 1) & 1, WAIT_POLLS);
             if (__any_sync(0xffffffffu, !ok)) {
                 failed = true;
                 break;
@@ -844,8 +861,14 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
                               make_float2(yy.x, yy.y));
                 }
             }
+            // all epilogue threads are done with the scratch and with this meta slot:
+            // refill the slot with the item two ahead
             tc::mbar_arrive(yfree);
-            tc::mbar_arrive(&metaempty[slot]);
+            if (!tc::mbar_wait(yfree, li & 1, WAIT_POLLS)) {
+                failed = true;
+                break;
+            }
+            if (it + 2 * (int64_t)gridDim.x < nwork) fill(it + 2 * (int64_t)gridDim.x, slot);
         }
     }
     if (failed) atomicOr(status, 4);
