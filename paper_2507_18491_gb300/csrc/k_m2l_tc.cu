@@ -701,11 +701,13 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
             const int cfirst = (int)((pg + V2_PG - (int)(g0 % V2_PG)) % V2_PG);
             const int nmine = cfirst < nchunk ? (nchunk - cfirst + V2_PG - 1) / V2_PG : 0;
             constexpr int KC = 4 * V2_KS;          // complex inputs per chunk
-            float2 pre[V2_D][KC];
+            constexpr int KH = KC / 2;             // of which this lane forms KH: kk = b*KH + h
+            float2 pre[V2_D][KH];
             // input (n', m') reads the expansion at (n', +-m'): index k or k - 2m'.
-            // The load itself is unconditional (from a clamped address) so that
-            // it stays in flight until its use V2_D chunks later; the mask is
-            // applied there.
+            // The two lanes of a column (Re row b = 0, Im row b = 1) each load and
+            // phase-shift half of the chunk's inputs and swap the products.
+            // Loads are unconditional (from a clamped address) so that they stay
+            // in flight until their use V2_D chunks later; the mask is applied there.
             static_assert(KC == 8, "one 16-byte load of the order table per chunk");
             const uint32_t mm0 = tc::smem_u32(MM);
             auto orders = [&](int ch, int(&mo)[KC]) {
@@ -714,13 +716,14 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
 #pragma unroll
                 for (int h = 0; h < KC; ++h) mo[h] = (int)(short)(wv[h >> 1] >> (16 * (h & 1)));
             };
-            auto fetch = [&](int ch, float2(&v)[KC]) {
+            auto fetch = [&](int ch, float2(&v)[KH]) {
                 int mo[KC];
                 orders(ch, mo);
 #pragma unroll
-                for (int h = 0; h < KC; ++h) {
-                    const int k = min(KC * ch + h, P - 1);
-                    const cf *a = valid ? src + (neg ? k - 2 * mo[h] : k) : me;
+                for (int h = 0; h < KH; ++h) {
+                    const int k = min(KC * ch + b * KH + h, P - 1);
+                    const int m = b ? mo[KH + h] : mo[h];
+                    const cf *a = valid ? src + (neg ? k - 2 * m : k) : me;
                     v[h] = *(const float2 *)a;
                 }
             };
@@ -741,30 +744,38 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
                     tc::fence_after();
                     int mo[KC];
                     orders(ch, mo);
+                    // this lane's half of the products (mine), then the partner's (other)
+                    cf mine[KH], other[KH];
 #pragma unroll
-                    for (int sub = 0; sub < V2_KS; ++sub) {
-                        uint32_t hi[8], lo[8];
-#pragma unroll
-                        for (int h = 0; h < 4; ++h) {
-                            const int k = KC * ch + 4 * sub + h;
-                            float yr = 0.f, yi = 0.f;
-                            if (valid && k < P) {
-                                const int m = mo[4 * sub + h];
-                                const float2 x = pre[u][4 * sub + h];
-                                const cf y = lds_cf(gr + 8 * (neg ? -m : m)) * cf{x.x, x.y};
-                                yr = y.x;
-                                yi = y.y;
-                            }
-                            const float a0 = b ? yi : yr, a1 = b ? yr : -yi;
-                            const float h0 = tc::tf32_round(a0), h1 = tc::tf32_round(a1);
-                            hi[2 * h] = __float_as_uint(h0);
-                            hi[2 * h + 1] = __float_as_uint(h1);
-                            lo[2 * h] = __float_as_uint(tc::tf32_round(a0 - h0));
-                            lo[2 * h + 1] = __float_as_uint(tc::tf32_round(a1 - h1));
+                    for (int h = 0; h < KH; ++h) {
+                        const int kk = b * KH + h;
+                        cf v{0.f, 0.f};
+                        if (valid && KC * ch + kk < P) {
+                            const int m = b ? mo[KH + h] : mo[h];
+                            v = lds_cf(gr + 8 * (neg ? -m : m)) * cf{pre[u][h].x, pre[u][h].y};
                         }
-                        tc::tmem_st8(lane_base + XB + 16 * (V2_KS * xs + sub), hi);
-                        tc::tmem_st8(lane_base + XB + 16 * (V2_KS * xs + sub) + 8, lo);
+                        mine[h] = v;
+                        other[h] = cf{__shfl_xor_sync(0xffffffffu, v.x, 1), __shfl_xor_sync(0xffffffffu, v.y, 1)};
                     }
+                    cf y[KC];
+#pragma unroll
+                    for (int h = 0; h < KH; ++h) {
+                        y[h] = b ? other[h] : mine[h];
+                        y[KH + h] = b ? mine[h] : other[h];
+                    }
+                    // tensor-memory slot: [hi | lo] of K-step 0, then of K-step 1
+                    uint32_t r32[32];
+#pragma unroll
+                    for (int kk = 0; kk < KC; ++kk) {
+                        const float a0 = b ? y[kk].y : y[kk].x, a1 = b ? y[kk].x : -y[kk].y;
+                        const float h0 = tc::tf32_round(a0), h1 = tc::tf32_round(a1);
+                        const int base = 16 * (kk >> 2) + 2 * (kk & 3);
+                        r32[base] = __float_as_uint(h0);
+                        r32[base + 1] = __float_as_uint(h1);
+                        r32[base + 8] = __float_as_uint(tc::tf32_round(a0 - h0));
+                        r32[base + 9] = __float_as_uint(tc::tf32_round(a1 - h1));
+                    }
+                    tc::tmem_st32(lane_base + XB + 16 * V2_KS * xs, r32);
                     tc::tmem_st_wait();
                     tc::fence_before();
                     tc::mbar_arrive(&xfull[xs]);
