@@ -38,6 +38,9 @@ struct DevState {
     int64_t *tchild = nullptr, *tparent = nullptr;
     GemmWork *gwork = nullptr;
     std::vector<int64_t> gwork_off;  // per child level: [off[l], off[l+1])
+    float *tupi = nullptr, *tdni = nullptr;   // persistent kernel: tiled translation matrices
+    M2LWork *twork = nullptr;        // persistent kernel: translation items, per child level
+    std::vector<int64_t> twork_off;
     NearPair *near = nullptr;
     cd *s2t = nullptr;               // near field: 8 combined coefficients per point pair
     S2TWork *s2twork = nullptr;      // near-field work items
@@ -567,6 +570,37 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
         }
         TRY(dupload(ctx, &d->tchild, ctx->tpair_child));
         TRY(dupload(ctx, &d->tparent, ctx->tpair_parent));
+        if (d->m2l_kernel == 3) {
+            // M2M / L2L on the persistent tensor-core kernel: tiled TF32 hi/lo images
+            // of the scaled FP64 matrices, items of 21 pairs (63 helical columns)
+            const size_t mf = tc2_matrix_floats(p);
+            std::vector<float> iu(ngr * mf), id(ngr * mf);
+            for (size_t i = 0; i < ngr; ++i) {
+                tile_matrix_tc2(p, &hup[i * P * P], &iu[i * mf]);
+                tile_matrix_tc2(p, &hdn[i * P * P], &id[i * mf]);
+            }
+            TRY(dupload(ctx, &d->tupi, iu));
+            TRY(dupload(ctx, &d->tdni, id));
+            std::vector<M2LWork> tw;
+            d->twork_off.assign(ctx->depth + 2, 0);
+            const int per = m2l_tc_cols() / 3;
+            for (int lev = 1; lev <= ctx->depth; ++lev) {
+                d->twork_off[lev] = (int64_t)tw.size();
+                for (size_t gi = 0; gi < ngr; ++gi) {
+                    const TransGroup &g = ctx->tgroups[gi];
+                    if (g.level != lev) continue;
+                    for (int64_t q = g.pair0; q < g.pair1; q += per) {
+                        M2LWork w{};
+                        w.geom = (int)gi;
+                        w.npair = (int)std::min<int64_t>(per, g.pair1 - q);
+                        w.pair0 = q;
+                        tw.push_back(w);
+                    }
+                }
+            }
+            d->twork_off[ctx->depth + 1] = (int64_t)tw.size();
+            TRY(dupload(ctx, &d->twork, tw));
+        }
         // work items per child level
         std::vector<GemmWork> gw;
         d->gwork_off.assign(ctx->depth + 2, 0);
@@ -647,6 +681,14 @@ static lmfmm_status matvec_t(lmfmm_ctx *ctx, const lmfmm_c128 *J, lmfmm_c128 *Ph
     launch_p2m<T>(p, d->nleaves, d->leaves, d->boxes, d->xyz, d->qh, ctx->med, d->lscale, me, st);
     CK(cudaEventRecord(d->ev[1], st));
     for (int lev = ctx->depth; lev >= 1; --lev) {
+        if constexpr (std::is_same<T, float>::value) {
+            if (d->m2l_kernel == 3) {
+                int64_t w0 = d->twork_off[lev], w1 = d->twork_off[lev + 1];
+                CK(launch_trans_tc2(p, w1 - w0, d->twork + w0, d->tchild, d->tparent, d->tupi, me, me, d->yscr,
+                                    d->nsm, d->mvstatus, st));
+                continue;
+            }
+        }
         int64_t w0 = d->gwork_off[lev], w1 = d->gwork_off[lev + 1];
         launch_group_gemm_t<T>(p, w1 - w0, d->gwork + w0, tup, d->tchild, d->tparent, me, me, true,
                                st);
@@ -669,6 +711,14 @@ static lmfmm_status matvec_t(lmfmm_ctx *ctx, const lmfmm_c128 *J, lmfmm_c128 *Ph
     }
     CK(cudaEventRecord(d->ev[3], st));
     for (int lev = 1; lev <= ctx->depth; ++lev) {
+        if constexpr (std::is_same<T, float>::value) {
+            if (d->m2l_kernel == 3) {
+                int64_t w0 = d->twork_off[lev], w1 = d->twork_off[lev + 1];
+                CK(launch_trans_tc2(p, w1 - w0, d->twork + w0, d->tparent, d->tchild, d->tdni, le, le, d->yscr,
+                                    d->nsm, d->mvstatus, st));
+                continue;
+            }
+        }
         int64_t w0 = d->gwork_off[lev], w1 = d->gwork_off[lev + 1];
         launch_group_gemm_t<T>(p, w1 - w0, d->gwork + w0, tdn, d->tparent, d->tchild, le, le, false,
                                st);

@@ -27,6 +27,7 @@
 // applies the output factors of the M2L and adds into the local expansion
 // with float2 atomics.
 #include <algorithm>
+#include <cstring>
 
 #include "kernels.cuh"
 #include "m2l_cols.cuh"
@@ -528,11 +529,41 @@ __device__ __forceinline__ void v2_fill_meta(int p, int P, const M2LWork &w, con
     }
 }
 
+// column data of a translation item (M2M or L2L): 3 columns (helical v) per
+// (source box, destination box) pair, unit factors, no index flips
+__device__ __forceinline__ void v2_fill_trans(int p, int P, const M2LWork &w, const int64_t *tsrc,
+                                              const int64_t *tdst, cf *G, cf *O, V2Col *cols, int tid, int nthr)
+{
+    const int MO = 2 * p + 1, ncol = 3 * w.npair;
+    for (int e = tid; e < BN * MO; e += nthr) {
+        G[e] = cf{1.f, 0.f};
+        O[e] = cf{1.f, 0.f};
+    }
+    for (int col = tid; col < BN; col += nthr) {
+        V2Col q{};
+        if (col < ncol) {
+            const int pp = col / 3, v = col - 3 * pp;
+            q.in_base = (tsrc[w.pair0 + pp] * 3 + v) * (int64_t)P;
+            q.out_base = (tdst[w.pair0 + pp] * 3 + v) * (int64_t)P;
+            q.pp = pp;
+            q.kap = 0;
+        }
+        cols[col] = q;
+    }
+}
+
+// complex columns of a work item
+__device__ __forceinline__ int v2_ncol(const M2LWork &w, int mode)
+{
+    return mode == 0 ? w.npair * ((w.t == 1) ? 1 : 2) : 3 * w.npair;
+}
+
 }  // namespace
 
 __global__ void __launch_bounds__(V2_THREADS, 1)
-    k_m2l_tc2(int p, int64_t nwork, const M2LWork *work, const GeomDev *geoms, const CompDev *comps,
-              const M2LPair *pairs, const cf *ephase, const float *timg, const cf *me, cf *le, float *yscr,
+    k_m2l_tc2(int p, int mode, int64_t nwork, const M2LWork *work, const GeomDev *geoms, const CompDev *comps,
+              const M2LPair *pairs, const cf *ephase, const int64_t *tsrc, const int64_t *tdst,
+              const float *timg, const cf *me, cf *le, float *yscr,
               int *status)
 {
     extern __shared__ __align__(1024) unsigned char smraw[];
@@ -594,7 +625,7 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
             int s = 0;
             for (int64_t it = blockIdx.x; it < nwork && !failed; it += gridDim.x) {
                 const M2LWork w = work[it];
-                const int64_t ti = geoms[w.geom].tab_index * NTAB + w.t;
+                const int64_t ti = mode == 0 ? geoms[w.geom].tab_index * NTAB + w.t : (int64_t)w.geom;
                 const unsigned char *src = (const unsigned char *)timg + (size_t)ti * nchunk * sp.CB;
                 for (int c = 0; c < nchunk; ++c) {
                     if (g >= (uint32_t)ST && !tc::mbar_wait(&tempty[s], ph ^ 1, WAIT_POLLS)) {
@@ -690,7 +721,7 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
                 failed = true;
                 break;
             }
-            const int ncol = w.npair * ((w.t == 1) ? 1 : 2);
+            const int ncol = v2_ncol(w, mode);
             const bool valid = cc < ncol;
             V2Col q{};
             if (valid) q = cols[cc];
@@ -799,11 +830,15 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
         // column data of item `it` into meta slot `slot`, then release it to the producers
         auto fill = [&](int64_t it, int slot) {
             const M2LWork w = work[it];
-            const CompDev c = comps[geoms[w.geom].comp];
-            const bool flip_in = (c.s < 0) != (c.has_src_refl != 0);
-            const bool flip_out = (c.s < 0) != (c.has_tgt_refl != 0);
-            v2_fill_meta(p, P, w, pairs, ephase, flip_in, flip_out, meta_G(slot), meta_O(slot), meta_cols(slot),
-                         ea, V2_ET);
+            if (mode == 0) {
+                const CompDev c = comps[geoms[w.geom].comp];
+                const bool flip_in = (c.s < 0) != (c.has_src_refl != 0);
+                const bool flip_out = (c.s < 0) != (c.has_tgt_refl != 0);
+                v2_fill_meta(p, P, w, pairs, ephase, flip_in, flip_out, meta_G(slot), meta_O(slot),
+                             meta_cols(slot), ea, V2_ET);
+            } else {
+                v2_fill_trans(p, P, w, tsrc, tdst, meta_G(slot), meta_O(slot), meta_cols(slot), ea, V2_ET);
+            }
             tc::mbar_arrive(&metafull[slot]);
         };
         for (int i = 0; i < 2; ++i)
@@ -836,7 +871,7 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
                 break;
             }
             const M2LWork w = work[it];
-            const int ncol = w.npair * ((w.t == 1) ? 1 : 2);
+            const int ncol = v2_ncol(w, mode);
             const cf *O = meta_O(slot);
             const V2Col *cols = meta_cols(slot);
             // outputs (column cc, row r) strided by V2_ET over the item; a batch
@@ -984,9 +1019,10 @@ void launch_tile_tables(int p, int64_t g0, int64_t ng, const GeomDev *geoms, con
     k_tile_tables<<<grid, 256, 0, st>>>(p, g0, ng, geoms, comps, tab64, img);
 }
 
-cudaError_t launch_m2l_tc2(int p, int64_t nwork, const M2LWork *work, const GeomDev *geoms,
-                           const CompDev *comps, const M2LPair *pairs, const cf *ephase, const float *img,
-                           const cf *me, cf *le, float *yscr, int nsm, int *status, cudaStream_t st)
+static cudaError_t launch_tc2(int p, int mode, int64_t nwork, const M2LWork *work, const GeomDev *geoms,
+                              const CompDev *comps, const M2LPair *pairs, const cf *ephase, const int64_t *tsrc,
+                              const int64_t *tdst, const float *img, const cf *in, cf *out, float *yscr, int nsm,
+                              int *status, cudaStream_t st)
 {
     if (nwork <= 0) return cudaSuccess;
     if (!m2l_tc2_supported(p) || nsm < 1) return cudaErrorInvalidValue;
@@ -994,9 +1030,62 @@ cudaError_t launch_m2l_tc2(int p, int64_t nwork, const M2LWork *work, const Geom
     // each CTA takes all 512 tensor-memory columns: ask for more than half of
     // an SM's shared memory so that no two CTAs are resident on one SM
     const size_t smem = std::max<size_t>(v2_plan(p).total, 116 * 1024);
-    k_m2l_tc2<<<(unsigned)grid, V2_THREADS, smem, st>>>(p, nwork, work, geoms, comps, pairs, ephase, img, me,
-                                                        le, yscr, status);
+    k_m2l_tc2<<<(unsigned)grid, V2_THREADS, smem, st>>>(p, mode, nwork, work, geoms, comps, pairs, ephase, tsrc,
+                                                        tdst, img, in, out, yscr, status);
     return cudaGetLastError();
+}
+
+cudaError_t launch_m2l_tc2(int p, int64_t nwork, const M2LWork *work, const GeomDev *geoms,
+                           const CompDev *comps, const M2LPair *pairs, const cf *ephase, const float *img,
+                           const cf *me, cf *le, float *yscr, int nsm, int *status, cudaStream_t st)
+{
+    return launch_tc2(p, 0, nwork, work, geoms, comps, pairs, ephase, nullptr, nullptr, img, me, le, yscr, nsm,
+                      status, st);
+}
+
+cudaError_t launch_trans_tc2(int p, int64_t nwork, const M2LWork *work, const int64_t *tsrc,
+                             const int64_t *tdst, const float *img, const cf *in, cf *out, float *yscr, int nsm,
+                             int *status, cudaStream_t st)
+{
+    return launch_tc2(p, 1, nwork, work, nullptr, nullptr, nullptr, nullptr, tsrc, tdst, img, in, out, yscr, nsm,
+                      status, st);
+}
+
+size_t tc2_matrix_floats(int p)
+{
+    const V2Plan sp = v2_plan(p);
+    return (size_t)sp.nchunk * sp.CB / sizeof(float);
+}
+
+// TF32 rounding on the host: to nearest, ties away from zero (as cvt.rna.tf32.f32)
+static float tf32_rna_host(float x)
+{
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    u = (u + 0x1000u) & 0xFFFFE000u;
+    float y;
+    std::memcpy(&y, &u, 4);
+    return y;
+}
+
+void tile_matrix_tc2(int p, const cd *M, float *img)
+{
+    const int P = (p + 1) * (p + 1);
+    const V2Plan sp = v2_plan(p);
+    const int NR = (int)sp.NR, nsub = (int)sp.nchunk * V2_KS;
+    for (int c = 0; c < nsub; ++c)
+        for (int r = 0; r < NR; ++r)
+            for (int kk = 0; kk < 8; ++kk) {
+                const int k = 4 * c + (kk >> 1);
+                double v = 0.0;
+                if (r < P && k < P) v = (kk & 1) ? M[(size_t)r * P + k].y : M[(size_t)r * P + k].x;
+                const float hi = tf32_rna_host((float)v);
+                const float lo = tf32_rna_host((float)(v - (double)hi));
+                const size_t base = (size_t)c * NR * 16;
+                const int off = ((r >> 3) * 256 + (kk >> 2) * 128 + (r & 7) * 16 + (kk & 3) * 4) >> 2;
+                img[base + off] = hi;
+                img[base + NR * 8 + off] = lo;
+            }
 }
 
 cudaError_t configure_m2l_tc()

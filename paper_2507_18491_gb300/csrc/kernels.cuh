@@ -113,6 +113,14 @@ void launch_tile_tables(int p, int64_t g0, int64_t ng, const GeomDev *geoms, con
 cudaError_t launch_m2l_tc2(int p, int64_t nwork, const M2LWork *work, const GeomDev *geoms,
                            const CompDev *comps, const M2LPair *pairs, const cf *ephase, const float *img,
                            const cf *me, cf *le, float *yscr, int nsm, int *status, cudaStream_t st);
+// M2M or L2L on the same kernel: items M2LWork{geom = translation group, t = 0,
+// npair, pair0} over pairs (tsrc[q], tdst[q]), 3 helical columns each; img holds
+// one tiled matrix per group (tile_matrix_tc2, tc2_matrix_floats(p) floats each)
+cudaError_t launch_trans_tc2(int p, int64_t nwork, const M2LWork *work, const int64_t *tsrc,
+                             const int64_t *tdst, const float *img, const cf *in, cf *out, float *yscr, int nsm,
+                             int *status, cudaStream_t st);
+size_t tc2_matrix_floats(int p);
+void tile_matrix_tc2(int p, const cd *M, float *img);   // host: P x P row-major (row = output index)
 template <typename T>
 void launch_scale_tables(int p, int64_t g0, int64_t ng, const GeomDev *geoms, const cd *tab64,
                          cx<T> *tab, cudaStream_t st);
