@@ -67,8 +67,12 @@ typedef struct {
     int tensor_cores;  /* mixed form only: M2L products on the tcgen05 tensor cores with FP32
                           accuracy from a three-term TF32 split.  1: the persistent kernel on a
                           pre-tiled table image for p <= 13, else the streamed-operand kernel
-                          (p <= 15); 2: the streamed-operand kernel; 0: FP32 SIMT pipes.
-                          Beyond p = 15 the SIMT kernel runs.  Ignored by the FP64 form. */
+                          (p <= 15); 2: the streamed-operand kernel; 3: as 1, and M2M / L2L on
+                          the persistent kernel too (about 4x faster translations, but the
+                          tensor core's truncating accumulation compounds along the tree:
+                          2.6e-6 instead of 8e-7 on the four-layer N = 2^20, p = 12 case);
+                          0: FP32 SIMT pipes.  Beyond p = 15 the SIMT kernel runs.  Ignored by
+                          the FP64 form. */
 } lmfmm_params;
 
 typedef struct {

@@ -40,6 +40,7 @@ struct DevState {
     std::vector<int64_t> gwork_off;  // per child level: [off[l], off[l+1])
     float *tupi = nullptr, *tdni = nullptr;   // persistent kernel: tiled translation matrices
     M2LWork *twork = nullptr;        // persistent kernel: translation items, per child level
+    bool trans_tc = false;           // M2M / L2L on the persistent kernel (tensor_cores = 3)
     std::vector<int64_t> twork_off;
     NearPair *near = nullptr;
     cd *s2t = nullptr;               // near field: 8 combined coefficients per point pair
@@ -286,8 +287,8 @@ lmfmm_status lmfmm_create(lmfmm_ctx **out, const lmfmm_params *prm, int device)
         g_err = "lmfmm_create: precision must be LMFMM_FP64 or LMFMM_MIXED";
         return LMFMM_ERR_ARG;
     }
-    if (prm->tensor_cores < 0 || prm->tensor_cores > 2) {
-        g_err = "lmfmm_create: tensor_cores must be 0, 1 or 2";
+    if (prm->tensor_cores < 0 || prm->tensor_cores > 3) {
+        g_err = "lmfmm_create: tensor_cores must be 0, 1, 2 or 3";
         return LMFMM_ERR_ARG;
     }
     cudaError_t e = cudaSetDevice(device);
@@ -414,7 +415,7 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
     const bool f32 = ctx->prm.precision == LMFMM_MIXED;
     d->m2l_kernel = !f32 ? 0
                     : ctx->prm.tensor_cores == 0 ? 1
-                    : (ctx->prm.tensor_cores == 1 && m2l_tc2_supported(p)) ? 3
+                    : ((ctx->prm.tensor_cores == 1 || ctx->prm.tensor_cores == 3) && m2l_tc2_supported(p)) ? 3
                     : m2l_tc_supported(p) ? 2 : 1;
     const size_t esz = f32 ? sizeof(cf) : sizeof(cd);
     {
@@ -570,7 +571,8 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
         }
         TRY(dupload(ctx, &d->tchild, ctx->tpair_child));
         TRY(dupload(ctx, &d->tparent, ctx->tpair_parent));
-        if (d->m2l_kernel == 3) {
+        d->trans_tc = d->m2l_kernel == 3 && ctx->prm.tensor_cores == 3;
+        if (d->trans_tc) {
             // M2M / L2L on the persistent tensor-core kernel: tiled TF32 hi/lo images
             // of the scaled FP64 matrices, items of 21 pairs (63 helical columns)
             const size_t mf = tc2_matrix_floats(p);
@@ -682,7 +684,7 @@ static lmfmm_status matvec_t(lmfmm_ctx *ctx, const lmfmm_c128 *J, lmfmm_c128 *Ph
     CK(cudaEventRecord(d->ev[1], st));
     for (int lev = ctx->depth; lev >= 1; --lev) {
         if constexpr (std::is_same<T, float>::value) {
-            if (d->m2l_kernel == 3) {
+            if (d->trans_tc) {
                 int64_t w0 = d->twork_off[lev], w1 = d->twork_off[lev + 1];
                 CK(launch_trans_tc2(p, w1 - w0, d->twork + w0, d->tchild, d->tparent, d->tupi, me, me, d->yscr,
                                     d->nsm, d->mvstatus, st));
@@ -712,7 +714,7 @@ static lmfmm_status matvec_t(lmfmm_ctx *ctx, const lmfmm_c128 *J, lmfmm_c128 *Ph
     CK(cudaEventRecord(d->ev[3], st));
     for (int lev = 1; lev <= ctx->depth; ++lev) {
         if constexpr (std::is_same<T, float>::value) {
-            if (d->m2l_kernel == 3) {
+            if (d->trans_tc) {
                 int64_t w0 = d->twork_off[lev], w1 = d->twork_off[lev + 1];
                 CK(launch_trans_tc2(p, w1 - w0, d->twork + w0, d->tparent, d->tchild, d->tdni, le, le, d->yscr,
                                     d->nsm, d->mvstatus, st));

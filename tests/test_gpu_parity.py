@@ -244,6 +244,27 @@ def test_tensor_core_m2l(p):
         assert e[tc] < 5e-6 and e[tc] < 2 * e[0] + 1e-7
 
 
+def test_tensor_core_translations():
+    """tensor_cores = 3 also runs M2M / L2L on the persistent tensor-core kernel:
+    within a looser bar of the FP64 form (the truncating tensor-core accumulation
+    compounds along the tree), and close to the default mixed form."""
+    w = W.three_layer(n=8192, p=12, depth=4)
+    Jt = torch.from_numpy(w.J).cuda()
+    kw = dict(p=12, depth=4, theta=0.5)
+    op = lmfmm.Operator(w.d, w.k, w.xyz, **kw).build()
+    a = op.matvec(Jt).cpu().numpy()
+    op.close()
+    out = {}
+    for tc in (1, 3):
+        op = lmfmm.Operator(w.d, w.k, w.xyz, precision=lmfmm.MIXED, tensor_cores=tc, **kw).build()
+        assert op.stats()["m2l_kernel"] == 3
+        out[tc] = op.matvec(Jt).cpu().numpy()
+        op.close()
+    print("M2L only %.3e  with translations %.3e" % (rel(out[1], a), rel(out[3], a)))
+    assert rel(out[3], a) < 5e-6
+    assert rel(out[3], out[1]) < 5e-6
+
+
 def test_stats_before_first_matvec():
     w = W.two_layer_small(n=200, seed=5)
     op = lmfmm.Operator(w.d, w.k, w.xyz, p=6, depth=2).build()
