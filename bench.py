@@ -39,13 +39,16 @@ FP64_PEAK_TFLOPS = SM_COUNT * 2 * 2 * SM_MHZ * 1e6 / 1e12
 TF32_PER_BF16 = 1.1 / 2.25
 
 
-def tf32_peak():
+def tensor_peak(tf32):
+    """Dense tensor peak of the kernel's operand type: the measured bf16 burst,
+    times the nominal tf32/bf16 ratio for a TF32 kernel."""
+    r, tag = (TF32_PER_BF16, " x nominal tf32/bf16 1.1/2.25") if tf32 else (1.0, "")
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             bf16 = float(json.load(f)["bf16_tflops"])
-        return bf16 * TF32_PER_BF16, "of measured: bf16 burst %.1f TFLOP/s x nominal tf32/bf16 1.1/2.25" % bf16
+        return bf16 * r, "of measured: bf16 burst %.1f TFLOP/s%s" % (bf16, tag)
     except (OSError, KeyError, ValueError):
-        return 1900.0 * TF32_PER_BF16, "of fallback: bf16 1900 TFLOP/s x nominal tf32/bf16 1.1/2.25"
+        return 1900.0 * r, "of fallback: bf16 1900 TFLOP/s%s" % tag
 
 
 def workload(name, seed_shift=0):
@@ -208,6 +211,8 @@ def main():
     ap.add_argument("--workload", default="four_layer")
     ap.add_argument("--p", type=int, default=0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--tensor-cores", type=int, default=None,
+                    help="tensor_cores option of the mixed form (default: the operator's)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -222,8 +227,9 @@ def main():
     p = args.p or w.p
     prec = lmfmm.FP64 if args.precision == "fp64" else lmfmm.MIXED
     t0 = time.time()
+    tck = {} if args.tensor_cores is None else {"tensor_cores": args.tensor_cores}
     op = lmfmm.Operator(w.d, w.k, w.xyz, p=p, depth=opt["depth"], theta=opt["theta"],
-                        precision=prec, device=dev).build()
+                        precision=prec, device=dev, **tck).build()
     setup_s = time.time() - t0
     stream = torch.cuda.current_stream()
     J = torch.from_numpy(w.J).to("cuda")
@@ -268,15 +274,14 @@ def main():
     achieved = flops / m2l_s / 1e12
     launches_per_step = 6 + 2 * st["depth"]
     kern = {0: "k_m2l<double>", 1: "k_m2l<float>", 2: "k_m2l_tc", 3: "k_m2l_tc2"}[st["m2l_kernel"]]
-    # DRAM bytes per launch of k_m2l_tc2: the table image times the read+write / image
-    # ratio of an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum = 5.23 GB for a
-    # 4.92 GB image, three-layer N = 8192, p = 12); other kernels: not captured
-    traffic = st["bytes_tables"] * (5.229 / 4.918) if st["m2l_kernel"] == 3 else None
+    # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum of an ncu
+    # capture): not yet captured for the bf16 three-piece form of k_m2l_tc2
+    traffic = None
     bound = "tensor" if st["m2l_kernel"] >= 2 else "alu"
     if prec == lmfmm.FP64:
         peak, peak_src = FP64_PEAK_TFLOPS, "derived FP64 ALU: 152 SM x 2 FMA/clk x 2 x 2070 MHz"
     elif bound == "tensor":
-        peak, peak_src = tf32_peak()
+        peak, peak_src = tensor_peak(tf32=st["m2l_kernel"] == 2)
     else:
         peak, peak_src = FP32_PEAK_TFLOPS, "derived FP32 ALU: 152 SM x 128 FMA/clk x 2 x 2070 MHz"
     line = {
@@ -285,7 +290,7 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if prec == lmfmm.FP64 else "f32", "data": "synthetic",
         "config": {"workload": w.name, "N": w.N, "layers": int(w.d.size + 1), "p": p,
-                   "depth": st["depth"], "theta": opt["theta"], "precision": args.precision,
+                   "depth": st["depth"], "theta": opt["theta"], "precision": args.precision, "tensor_cores": int(args.tensor_cores if args.tensor_cores is not None else 1),
                    "components": st["n_components"], "m2l_pairs": st["n_m2l_pairs"],
                    "geometries": st["n_geometries"], "near_point_pairs": st["n_near_point_pairs"],
                    "setup_s": round(setup_s, 3), "l2": "flushed (256 MiB write) between steps",
@@ -299,7 +304,8 @@ def main():
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_source": peak_src, "flops_per_launch": flops,
                      "flops_definition": "algorithmic: 8 P^2 real flops per M2L column (complex P x P "
-                                         "product); the tensor path executes 3 TF32 terms of each"},
+                                         "product); the tensor path executes more: 6 bf16 products of "
+                                         "three-piece splits (k_m2l_tc2) or 3 TF32 terms (k_m2l_tc)"},
     }
     if rank == 0 and not args.no_cpu:
         line["config"]["rel_err_vs_oracle"] = accuracy(op, w)

@@ -38,7 +38,7 @@ struct DevState {
     int64_t *tchild = nullptr, *tparent = nullptr;
     GemmWork *gwork = nullptr;
     std::vector<int64_t> gwork_off;  // per child level: [off[l], off[l+1])
-    float *tupi = nullptr, *tdni = nullptr;   // persistent kernel: tiled translation matrices
+    void *tupi = nullptr, *tdni = nullptr;    // persistent kernel: tiled translation matrices (bf16 x 3)
     M2LWork *twork = nullptr;        // persistent kernel: translation items, per child level
     bool trans_tc = false;           // M2M / L2L on the persistent kernel (tensor_cores = 3)
     std::vector<int64_t> twork_off;
@@ -466,8 +466,8 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
         TRY(tabulate(ctx, hg, d->comps, dG, dcg, tab64, st));
         TRY(dupload(ctx, &d->geoms, hg));
         if (d->m2l_kernel == 3) {
-            float *img = nullptr;
-            TRY(dalloc(ctx, &img, m2l_tc2_image_bytes(p, (int64_t)hg.size()) / sizeof(float)));
+            unsigned char *img = nullptr;
+            TRY(dalloc(ctx, &img, m2l_tc2_image_bytes(p, (int64_t)hg.size())));
             launch_tile_tables(p, 0, (int64_t)hg.size(), d->geoms, d->comps, tab64, img, st);
             CK(cudaGetLastError());
             CK(cudaStreamSynchronize(st));
@@ -509,6 +509,11 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
     int64_t ncols = 0;
     for (size_t gi = 0; gi < ctx->geoms.size(); ++gi) {
         const Geom &g = ctx->geoms[gi];
+        const CompDev &cg = ctx->comps[g.comp];
+        // image maps of the component: the sign of odd degrees flips when the
+        // source (target) side is mirrored an odd number of times
+        const int flags = (((cg.s < 0) != (cg.has_src_refl != 0)) ? 1 : 0) |
+                          (((cg.s < 0) != (cg.has_tgt_refl != 0)) ? 2 : 0);
         for (int t = 0; t < NTAB; ++t) {
             int bn = d->m2l_kernel >= 2 ? m2l_tc_cols() : f32 ? gemm_cols<float>() : gemm_cols<double>();
             int per = (t == 1) ? bn : bn / 2;
@@ -516,6 +521,7 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
                 M2LWork w{};
                 w.geom = (int)gi;
                 w.t = t;
+                w.flags = flags;
                 w.pair0 = q;
                 w.npair = (int)std::min<int64_t>(per, g.pair1 - q);
                 ncols += w.npair * (t == 1 ? 1 : 2);
@@ -573,16 +579,19 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
         TRY(dupload(ctx, &d->tparent, ctx->tpair_parent));
         d->trans_tc = d->m2l_kernel == 3 && ctx->prm.tensor_cores == 3;
         if (d->trans_tc) {
-            // M2M / L2L on the persistent tensor-core kernel: tiled TF32 hi/lo images
-            // of the scaled FP64 matrices, items of 21 pairs (63 helical columns)
-            const size_t mf = tc2_matrix_floats(p);
-            std::vector<float> iu(ngr * mf), id(ngr * mf);
+            // M2M / L2L on the persistent tensor-core kernel: tiled bf16 three-piece
+            // images of the scaled FP64 matrices, items of 21 pairs (63 helical columns)
+            const size_t mw = tc2_matrix_bytes(p) / 4;
+            std::vector<uint32_t> iu(ngr * mw), id(ngr * mw);
             for (size_t i = 0; i < ngr; ++i) {
-                tile_matrix_tc2(p, &hup[i * P * P], &iu[i * mf]);
-                tile_matrix_tc2(p, &hdn[i * P * P], &id[i * mf]);
+                tile_matrix_tc2(p, &hup[i * P * P], &iu[i * mw]);
+                tile_matrix_tc2(p, &hdn[i * P * P], &id[i * mw]);
             }
-            TRY(dupload(ctx, &d->tupi, iu));
-            TRY(dupload(ctx, &d->tdni, id));
+            uint32_t *a1 = nullptr, *a2 = nullptr;
+            TRY(dupload(ctx, &a1, iu));
+            TRY(dupload(ctx, &a2, id));
+            d->tupi = a1;
+            d->tdni = a2;
             std::vector<M2LWork> tw;
             d->twork_off.assign(ctx->depth + 2, 0);
             const int per = m2l_tc_cols() / 3;
@@ -686,8 +695,8 @@ static lmfmm_status matvec_t(lmfmm_ctx *ctx, const lmfmm_c128 *J, lmfmm_c128 *Ph
         if constexpr (std::is_same<T, float>::value) {
             if (d->trans_tc) {
                 int64_t w0 = d->twork_off[lev], w1 = d->twork_off[lev + 1];
-                CK(launch_trans_tc2(p, w1 - w0, d->twork + w0, d->tchild, d->tparent, d->tupi, me, me, d->yscr,
-                                    d->nsm, d->mvstatus, st));
+                CK(launch_trans_tc2(p, w1 - w0, d->twork + w0, d->tchild, d->tparent, d->tupi, me, me,
+                                    d->yscr, d->nsm, d->mvstatus, st));
                 continue;
             }
         }
@@ -698,9 +707,10 @@ static lmfmm_status matvec_t(lmfmm_ctx *ctx, const lmfmm_c128 *J, lmfmm_c128 *Ph
     CK(cudaEventRecord(d->ev[2], st));
     CK(cudaMemsetAsync(le, 0, (size_t)nbox * 3 * P * sizeof(cx<T>), st));
     if constexpr (std::is_same<T, float>::value) {
-        if (d->m2l_kernel == 3)
-            CK(launch_m2l_tc2(p, d->n_m2lwork, d->m2lwork, d->geoms, d->comps, d->m2l,
-                              d->ephase, (const float *)d->tab, me, le, d->yscr, d->nsm, d->mvstatus, st));
+        if (d->m2l_kernel == 3) {
+            CK(launch_m2l_tc2(p, d->n_m2lwork, d->m2lwork, d->geoms, d->m2l, d->ephase, d->tab,
+                              me, le, d->yscr, d->nsm, d->mvstatus, st));
+        }
         else if (d->m2l_kernel == 2)
             CK(launch_m2l_tc(p, d->n_m2lwork, d->m2lwork, d->geoms, d->comps, d->m2l,
                              (const cf *)d->tab, me, le, d->mvstatus, st));
@@ -716,8 +726,8 @@ static lmfmm_status matvec_t(lmfmm_ctx *ctx, const lmfmm_c128 *J, lmfmm_c128 *Ph
         if constexpr (std::is_same<T, float>::value) {
             if (d->trans_tc) {
                 int64_t w0 = d->twork_off[lev], w1 = d->twork_off[lev + 1];
-                CK(launch_trans_tc2(p, w1 - w0, d->twork + w0, d->tparent, d->tchild, d->tdni, le, le, d->yscr,
-                                    d->nsm, d->mvstatus, st));
+                CK(launch_trans_tc2(p, w1 - w0, d->twork + w0, d->tparent, d->tchild, d->tdni, le, le,
+                                    d->yscr, d->nsm, d->mvstatus, st));
                 continue;
             }
         }

@@ -27,7 +27,11 @@
 // applies the output factors of the M2L and adds into the local expansion
 // with float2 atomics.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
+#include <vector>
+
+#include <cuda_bf16.h>
 
 #include "kernels.cuh"
 #include "m2l_cols.cuh"
@@ -394,14 +398,19 @@ __global__ void __launch_bounds__(NT) k_m2l_tc(int p, int MT, uint32_t tmem_cols
 // bit 4 of the status word and its role stops.
 namespace {
 
-constexpr int V2_KS = 2;           // MMA K-steps (8 real K each) per ring chunk
-constexpr int V2_SX = 3;           // X ring slots (tensor memory, 16 * V2_KS columns each)
+constexpr int V2_KS = 2;           // MMA K-steps (16 real K each) per ring chunk
+constexpr int V2_KC = 8 * V2_KS;   // complex inputs per ring chunk
+constexpr int V2_NPC = 3;          // bf16 pieces per value
+constexpr int V2_XW = 8 * V2_NPC * V2_KS;   // tensor-memory columns of an X chunk
+constexpr int V2_SX = 3;           // X ring slots
 constexpr int V2_ST_MAX = 16;      // table ring slots (shared memory)
 constexpr int V2_PG = 2;           // producer groups (alternate chunks)
 constexpr int V2_D = 2;            // chunks of a group prefetched into registers
-constexpr int V2_NR_MAX = 208;     // table rows padded to 16: p <= 13
+constexpr int V2_NR_MAX = 176;     // table rows padded to 16: 2 NR + V2_SX V2_XW <= 512, p <= 12
 constexpr int V2_PT = 128 * V2_PG; // producer threads
 constexpr int V2_ET = 256;         // epilogue threads
+constexpr int V2_EW = V2_ET / 32;  // epilogue warps
+constexpr int V2_RJ = (V2_NR_MAX + 31) / 32;   // rows per lane of a column in the scatter
 constexpr int V2_WTMA = (V2_PT + V2_ET) / 32, V2_WMMA = V2_WTMA + 1;
 constexpr int V2_THREADS = (V2_WMMA + 1) * 32;
 constexpr uint32_t V2_SMEM_MAX = 227 * 1024;
@@ -412,7 +421,7 @@ struct V2Col {
 };
 
 struct V2Plan {
-    uint32_t NR, nchunk, SB, CB, ST, MO, g_bytes, meta_bytes, meta, tabs, mm_n, bars, total;
+    uint32_t NR, nchunk, SB, CB, ST, MO, g_bytes, cols_bytes, meta_bytes, meta, tabs, mm_n, bars, total;
 };
 
 __host__ __device__ inline V2Plan v2_plan(int p)
@@ -420,13 +429,14 @@ __host__ __device__ inline V2Plan v2_plan(int p)
     const int P = (p + 1) * (p + 1);
     V2Plan s;
     s.NR = (uint32_t)((P + 15) & ~15);
-    s.nchunk = (uint32_t)(((P + 3) / 4 + V2_KS - 1) / V2_KS);   // chunks of V2_KS K-steps
-    s.SB = s.NR * 64;                               // hi + lo image of a K-step: NR rows x 8 tf32 x 2
+    s.nchunk = (uint32_t)(((P + 7) / 8 + V2_KS - 1) / V2_KS);   // chunks of V2_KS K-steps
+    s.SB = s.NR * 32 * V2_NPC;                      // image of a K-step: V2_NPC planes of NR rows x 16 bf16
     s.CB = V2_KS * s.SB;
     s.MO = 2 * p + 1;                               // orders -p..p
     s.g_bytes = BN * s.MO * 8;                      // one factor table: [64][2p+1] complex
-    s.meta_bytes = 2 * s.g_bytes + BN * (uint32_t)sizeof(V2Col);
-    s.mm_n = 4 * V2_KS * s.nchunk;                  // order table, whole chunks (>= P)
+    s.cols_bytes = BN * (uint32_t)sizeof(V2Col);
+    s.meta_bytes = 2 * s.g_bytes + s.cols_bytes;    // G, O, column records
+    s.mm_n = V2_KC * s.nchunk;                      // order table, whole chunks (>= P)
     const uint32_t fixed = 2 * s.meta_bytes + 2 * s.mm_n + 32 + (2 * V2_ST_MAX + 2 * V2_SX + 12) * 8 + 16;
     uint32_t st = (V2_SMEM_MAX - fixed) / s.CB;
     s.ST = st > V2_ST_MAX ? V2_ST_MAX : st;
@@ -448,6 +458,23 @@ __device__ __forceinline__ uint4 lds_u4(uint32_t a)
     uint4 v;
     asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
     return v;
+}
+
+// three-piece bf16 split of a pair, x ~ b1 + b2 + b3 per component (b1 =
+// bf16(x), b2 = bf16(x - b1), b3 = bf16(x - b1 - b2): 24 significant bits,
+// FP32's exponent range); word j holds piece j, lo in the low half
+__device__ __forceinline__ void v2_split_bf16(float lo, float hi, uint32_t (&w)[V2_NPC])
+{
+    float2 r{lo, hi};
+#pragma unroll
+    for (int j = 0; j < V2_NPC; ++j) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(r.x, r.y);
+        w[j] = *(const uint32_t *)&h;
+        if (j + 1 < V2_NPC) {
+            const float2 f = __bfloat1622float2(h);
+            r = float2{r.x - f.x, r.y - f.y};
+        }
+    }
 }
 
 // i^k v, exact
@@ -476,23 +503,17 @@ __device__ __forceinline__ void v2_fill_meta(int p, int P, const M2LWork &w, con
     const int t = w.t, ncpp = (t == 1) ? 1 : 2, ncol = w.npair * ncpp;
     const int lane = tid & 31, wi = tid >> 5, nw = nthr >> 5;
     const int m = lane - p;                      // order of this lane
-    // rows per warp: at most RB (npair, ncol <= 64 over nw >= 8 warps); all
-    // loads of a warp are issued before the first use
+    // rows per warp: at most RB (npair, ncol <= 64 over nw >= 8 warps); every
+    // global load of the fill is issued before the first use
     constexpr int RB = 8;
+    M2LPair pr{};
+    if (tid < ncol) pr = pairs[w.pair0 + (ncpp == 1 ? tid : tid >> 1)];
+    cf vg[RB], vo[RB];
     if (lane < MO) {
-        cf v[RB];
 #pragma unroll
         for (int i = 0; i < RB; ++i) {
             const int pp = min(wi + i * nw, w.npair - 1);
-            v[i] = ephase[(w.pair0 + pp) * MW + (p + 2) + m];
-        }
-#pragma unroll
-        for (int i = 0; i < RB; ++i) {
-            const int pp = wi + i * nw;
-            if (pp >= w.npair) break;
-            cf x = mul_ipow(m, v[i]);
-            if (flip_in && (m & 1)) x = -x;
-            G[pp * MO + lane] = x;
+            vg[i] = ephase[(w.pair0 + pp) * MW + (p + 2) + m];
         }
 #pragma unroll
         for (int i = 0; i < RB; ++i) {
@@ -500,7 +521,15 @@ __device__ __forceinline__ void v2_fill_meta(int p, int P, const M2LWork &w, con
             const int pp = ncpp == 1 ? col : col >> 1;
             const ColSpec &cs = c_cols[t][ncpp == 1 ? 0 : col & 1];
             const int mu = cs.kap < 0 ? -m : m;
-            v[i] = ephase[(w.pair0 + pp) * MW + (p + 2) + cs.kap - mu];
+            vo[i] = ephase[(w.pair0 + pp) * MW + (p + 2) + cs.kap - mu];
+        }
+#pragma unroll
+        for (int i = 0; i < RB; ++i) {
+            const int pp = wi + i * nw;
+            if (pp >= w.npair) break;
+            cf x = mul_ipow(m, vg[i]);
+            if (flip_in && (m & 1)) x = -x;
+            G[pp * MO + lane] = x;
         }
 #pragma unroll
         for (int i = 0; i < RB; ++i) {
@@ -511,26 +540,23 @@ __device__ __forceinline__ void v2_fill_meta(int p, int P, const M2LWork &w, con
             float cf0 = (float)cs.coef;
             if (cs.kap < 0 && (cs.kap & 1)) cf0 = -cf0;
             if (flip_out && (mu & 1)) cf0 = -cf0;
-            O[col * MO + lane] = cf0 * mul_ipow(1 + cs.kap - mu, v[i]);
+            O[col * MO + lane] = cf0 * mul_ipow(1 + cs.kap - mu, vo[i]);
         }
     }
-    for (int col = tid; col < BN; col += nthr) {
+    static_assert(BN <= V2_ET, "one column record per epilogue thread");
+    if (tid < BN) {
         V2Col q{};
-        if (col < ncol) {
-            const int pp = ncpp == 1 ? col : col >> 1;
-            const ColSpec &cs = c_cols[t][ncpp == 1 ? 0 : col & 1];
-            const M2LPair pr = pairs[w.pair0 + pp];
+        if (tid < ncol) {
+            const ColSpec &cs = c_cols[t][ncpp == 1 ? 0 : tid & 1];
             q.in_base = (pr.src * 3 + cs.vin) * (int64_t)P;
             q.out_base = (pr.tgt * 3 + cs.vout) * (int64_t)P;
-            q.pp = pp;
+            q.pp = ncpp == 1 ? tid : tid >> 1;
             q.kap = cs.kap;
         }
-        cols[col] = q;
+        cols[tid] = q;
     }
 }
 
-// column data of a translation item (M2M or L2L): 3 columns (helical v) per
-// (source box, destination box) pair, unit factors, no index flips
 __device__ __forceinline__ void v2_fill_trans(int p, int P, const M2LWork &w, const int64_t *tsrc,
                                               const int64_t *tdst, cf *G, cf *O, V2Col *cols, int tid, int nthr)
 {
@@ -561,9 +587,8 @@ __device__ __forceinline__ int v2_ncol(const M2LWork &w, int mode)
 }  // namespace
 
 __global__ void __launch_bounds__(V2_THREADS, 1)
-    k_m2l_tc2(int p, int mode, int64_t nwork, const M2LWork *work, const GeomDev *geoms, const CompDev *comps,
-              const M2LPair *pairs, const cf *ephase, const int64_t *tsrc, const int64_t *tdst,
-              const float *timg, const cf *me, cf *le, float *yscr,
+    k_m2l_tc2(int p, int mode, int64_t nwork, const M2LWork *work, const GeomDev *geoms, const M2LPair *pairs, const cf *ephase, const int64_t *tsrc, const int64_t *tdst,
+              const uint32_t *timg, const cf *me, cf *le, float *yscr,
               int *status)
 {
     extern __shared__ __align__(1024) unsigned char smraw[];
@@ -582,7 +607,8 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
     auto meta_cols = [&](int slot) {
         return (V2Col *)(smraw + sp.meta + slot * sp.meta_bytes + 2 * sp.g_bytes);
     };
-    float *Y = yscr + (size_t)blockIdx.x * NR * 128;   // [r][real column]
+
+    float *Y = yscr + (size_t)blockIdx.x * NR * 128;   // [complex column][r], complex
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t XB = 2 * (uint32_t)NR;              // tensor-memory column of the X ring
 
@@ -648,11 +674,11 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
     } else if (warp == V2_WMMA) {
         // ------------------------------------------------ MMA issue
         if (lane == 0) {
-            const uint32_t idesc = tc::idesc_tf32(128, NR, false);
+            const uint32_t idesc = tc::idesc_bf16(128, NR);
             // descriptor of ring slot 0; the address field counts 16-byte units,
             // so slot, K-step and lo-plane offsets add to it directly
             const uint64_t dring0 = tc::sdesc(tc::smem_u32(smraw), 128, 256);
-            const uint64_t d_cb = sp.CB >> 4, d_sb = sp.SB >> 4, d_lo = (uint32_t)(NR * 32) >> 4;
+            const uint64_t d_cb = sp.CB >> 4, d_sb = sp.SB >> 4, d_pl = (uint32_t)(NR * 32) >> 4;
             uint64_t dslot = dring0;                       // descriptor of table slot st
             uint32_t aslot = tbase + XB;                   // tensor-memory address of X slot sx
             uint32_t li = 0, tph = 0, xph = 0;
@@ -671,17 +697,21 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
                     tc::fence_after();
 #pragma unroll
                     for (int u = 0; u < V2_KS; ++u) {
-                        const uint32_t ahi = aslot + 16 * u, alo = ahi + 8;
-                        const uint64_t dbh = dslot + u * d_sb, dbl = dbh + d_lo;
+                        // pieces 1, 2, 3 of X (tensor memory) and of the table (shared memory)
+                        const uint32_t a1 = aslot + 8 * V2_NPC * u, a2 = a1 + 8, a3 = a1 + 16;
+                        const uint64_t b1 = dslot + u * d_sb, b2 = b1 + d_pl, b3 = b2 + d_pl;
                         const uint32_t acc = (c > 0 || u > 0) ? 1u : 0u;
-                        tc::mma_tf32_ta(tbase, ahi, dbh, idesc, acc);
-                        tc::mma_tf32_ta(tbase + NR, ahi, dbl, idesc, acc);
-                        tc::mma_tf32_ta(tbase + NR, alo, dbh, idesc, 1u);
+                        tc::mma_f16_ta(tbase, a1, b1, idesc, acc);        // 1 x 1: large accumulator
+                        tc::mma_f16_ta(tbase + NR, a1, b2, idesc, acc);   // the rest: small accumulator
+                        tc::mma_f16_ta(tbase + NR, a2, b1, idesc, 1u);
+                        tc::mma_f16_ta(tbase + NR, a1, b3, idesc, 1u);
+                        tc::mma_f16_ta(tbase + NR, a2, b2, idesc, 1u);
+                        tc::mma_f16_ta(tbase + NR, a3, b1, idesc, 1u);
                     }
                     tc::commit(&tempty[st]);
                     tc::commit(&xempty[sx]);
                     dslot += d_cb;
-                    aslot += 16 * V2_KS;
+                    aslot += V2_XW;
                     if (++st == ST) {
                         st = 0;
                         tph ^= 1;
@@ -731,7 +761,7 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
             // this group's chunks of the item: c = cfirst, cfirst + V2_PG, ...
             const int cfirst = (int)((pg + V2_PG - (int)(g0 % V2_PG)) % V2_PG);
             const int nmine = cfirst < nchunk ? (nchunk - cfirst + V2_PG - 1) / V2_PG : 0;
-            constexpr int KC = 4 * V2_KS;          // complex inputs per chunk
+            constexpr int KC = V2_KC;              // complex inputs per chunk
             constexpr int KH = KC / 2;             // of which this lane forms KH: kk = b*KH + h
             float2 pre[V2_D][KH];
             // input (n', m') reads the expansion at (n', +-m'): index k or k - 2m'.
@@ -739,13 +769,16 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
             // phase-shift half of the chunk's inputs and swap the products.
             // Loads are unconditional (from a clamped address) so that they stay
             // in flight until their use V2_D chunks later; the mask is applied there.
-            static_assert(KC == 8, "one 16-byte load of the order table per chunk");
+            static_assert(KC == 16, "two 16-byte loads of the order table per chunk");
             const uint32_t mm0 = tc::smem_u32(MM);
             auto orders = [&](int ch, int(&mo)[KC]) {
-                const uint4 q4 = lds_u4(mm0 + 2 * KC * ch);
-                const uint32_t wv[4] = {q4.x, q4.y, q4.z, q4.w};
 #pragma unroll
-                for (int h = 0; h < KC; ++h) mo[h] = (int)(short)(wv[h >> 1] >> (16 * (h & 1)));
+                for (int q2 = 0; q2 < 2; ++q2) {
+                    const uint4 q4 = lds_u4(mm0 + 2 * KC * ch + 16 * q2);
+                    const uint32_t wv[4] = {q4.x, q4.y, q4.z, q4.w};
+#pragma unroll
+                    for (int h = 0; h < 8; ++h) mo[8 * q2 + h] = (int)(short)(wv[h >> 1] >> (16 * (h & 1)));
+                }
             };
             auto fetch = [&](int ch, float2(&v)[KH]) {
                 int mo[KC];
@@ -775,8 +808,8 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
                     tc::fence_after();
                     int mo[KC];
                     orders(ch, mo);
-                    // this lane's half of the products (mine), then the partner's (other)
-                    cf mine[KH], other[KH];
+                    // this lane's half of the products; the partner's half comes by shuffle
+                    cf mine[KH];
 #pragma unroll
                     for (int h = 0; h < KH; ++h) {
                         const int kk = b * KH + h;
@@ -786,27 +819,35 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
                             v = lds_cf(gr + 8 * (neg ? -m : m)) * cf{pre[u][h].x, pre[u][h].y};
                         }
                         mine[h] = v;
-                        other[h] = cf{__shfl_xor_sync(0xffffffffu, v.x, 1), __shfl_xor_sync(0xffffffffu, v.y, 1)};
                     }
-                    cf y[KC];
+                    // tensor-memory slot: per K-step of 16 real K (8 inputs) 8 columns of
+                    // bf16 pairs for each of the 3 pieces; input kk -> (row 2c: Re, -Im;
+                    // row 2c+1: Im, Re), even K in the low half
+                    // One K-step at a time (24 words live), stores aligned to their width.
+                    static_assert(V2_KS == 2 && V2_NPC == 3, "two K-steps of 24 columns per chunk");
 #pragma unroll
-                    for (int h = 0; h < KH; ++h) {
-                        y[h] = b ? other[h] : mine[h];
-                        y[KH + h] = b ? mine[h] : other[h];
-                    }
-                    // tensor-memory slot: [hi | lo] of K-step 0, then of K-step 1
-                    uint32_t r32[32];
+                    for (int st = 0; st < V2_KS; ++st) {
+                        const bool own = (st == 0) == (b == 0);
+                        uint32_t rw[8 * V2_NPC];
 #pragma unroll
-                    for (int kk = 0; kk < KC; ++kk) {
-                        const float a0 = b ? y[kk].y : y[kk].x, a1 = b ? y[kk].x : -y[kk].y;
-                        const float h0 = tc::tf32_round(a0), h1 = tc::tf32_round(a1);
-                        const int base = 16 * (kk >> 2) + 2 * (kk & 3);
-                        r32[base] = __float_as_uint(h0);
-                        r32[base + 1] = __float_as_uint(h1);
-                        r32[base + 8] = __float_as_uint(tc::tf32_round(a0 - h0));
-                        r32[base + 9] = __float_as_uint(tc::tf32_round(a1 - h1));
+                        for (int i = 0; i < 8; ++i) {
+                            const cf o{__shfl_xor_sync(0xffffffffu, mine[i].x, 1),
+                                       __shfl_xor_sync(0xffffffffu, mine[i].y, 1)};
+                            const cf y = own ? mine[i] : o;
+                            uint32_t w[V2_NPC];
+                            v2_split_bf16(b ? y.y : y.x, b ? y.x : -y.y, w);
+#pragma unroll
+                            for (int pc = 0; pc < V2_NPC; ++pc) rw[i + 8 * pc] = w[pc];
+                        }
+                        const uint32_t ta = lane_base + XB + V2_XW * xs + 8 * V2_NPC * st;
+                        if (st == 0) {
+                            tc::tmem_st16(ta, rw);
+                            tc::tmem_st8(ta + 16, rw + 16);
+                        } else {
+                            tc::tmem_st8(ta, rw);
+                            tc::tmem_st16(ta + 8, rw + 8);
+                        }
                     }
-                    tc::tmem_st32(lane_base + XB + 16 * V2_KS * xs, r32);
                     tc::tmem_st_wait();
                     tc::fence_before();
                     tc::mbar_arrive(&xfull[xs]);
@@ -827,24 +868,27 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
         const int q4 = warp & 3, half = ea / 128;     // lane quadrant, slab parity
         const int e = 32 * q4 + lane;                 // real column = tensor-memory lane
         const uint32_t lane_base = tbase + ((uint32_t)(32 * q4) << 16);
-        // column data of item `it` into meta slot `slot`, then release it to the producers
-        auto fill = [&](int64_t it, int slot) {
-            const M2LWork w = work[it];
-            if (mode == 0) {
-                const CompDev c = comps[geoms[w.geom].comp];
-                const bool flip_in = (c.s < 0) != (c.has_src_refl != 0);
-                const bool flip_out = (c.s < 0) != (c.has_tgt_refl != 0);
-                v2_fill_meta(p, P, w, pairs, ephase, flip_in, flip_out, meta_G(slot), meta_O(slot),
-                             meta_cols(slot), ea, V2_ET);
-            } else {
+        const int ew = ea >> 5;                       // epilogue warp 0 .. V2_EW-1
+        int rm[V2_RJ];                                // order m of rows lane + 32 i
+#pragma unroll
+        for (int i = 0; i < V2_RJ; ++i) rm[i] = MM[min(lane + 32 * i, P - 1)];
+        // column data of item w into meta slot `slot`, then release it to the producers
+        auto fill = [&](const M2LWork &w, int slot) {
+            if (mode == 0)
+                v2_fill_meta(p, P, w, pairs, ephase, (w.flags & 1) != 0, (w.flags & 2) != 0, meta_G(slot),
+                             meta_O(slot), meta_cols(slot), ea, V2_ET);
+            else
                 v2_fill_trans(p, P, w, tsrc, tdst, meta_G(slot), meta_O(slot), meta_cols(slot), ea, V2_ET);
-            }
             tc::mbar_arrive(&metafull[slot]);
         };
         for (int i = 0; i < 2; ++i)
-            if (blockIdx.x + (int64_t)i * gridDim.x < nwork) fill(blockIdx.x + (int64_t)i * gridDim.x, i);
+            if (blockIdx.x + (int64_t)i * gridDim.x < nwork) fill(work[blockIdx.x + (int64_t)i * gridDim.x], i);
         uint32_t li = 0;
         for (int64_t it = blockIdx.x; it < nwork && !failed; it += gridDim.x, ++li) {
+            // descriptor of the item two ahead, read now and used after the scatter
+            const int64_t itn = it + 2 * (int64_t)gridDim.x;
+            const M2LWork wn = work[min(itn, nwork - 1)];
+            const M2LWork wc = work[it];
             const int slot = li & 1;
             bool ok = tc::mbar_wait(accfull, li & 1, WAIT_POLLS);
             if (__any_sync(0xffffffffu, !ok)) {
@@ -852,14 +896,27 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
                 break;
             }
             tc::fence_after();
+            // scratch layout [column cc][row r] complex: the two lanes of a column
+            // swap values so that each store of the pair fills one 32-byte sector
+            // (lane b writes rows 4j + 2b, 4j + 2b + 1 of the slab)
+            const int b = lane & 1;
+            float2 *Yc = (float2 *)Y + (size_t)(e >> 1) * NR;
             for (int c0 = 16 * half; c0 < NR; c0 += 32) {   // NR is a multiple of 16
                 uint32_t va[16], vb[16];
                 tc::tmem_ld16(lane_base + c0, va);
                 tc::tmem_ld16(lane_base + NR + c0, vb);
                 tc::tmem_ld_wait();
+                float v[16];
 #pragma unroll
-                for (int i = 0; i < 16; ++i)
-                    Y[(size_t)(c0 + i) * 128 + e] = __uint_as_float(va[i]) + __uint_as_float(vb[i]);
+                for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(va[i]) + __uint_as_float(vb[i]);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float r0 = __shfl_xor_sync(0xffffffffu, b ? v[4 * j] : v[4 * j + 2], 1);
+                    const float r1 = __shfl_xor_sync(0xffffffffu, b ? v[4 * j + 1] : v[4 * j + 3], 1);
+                    const float4 o = b ? make_float4(r0, v[4 * j + 2], r1, v[4 * j + 3])
+                                       : make_float4(v[4 * j], r0, v[4 * j + 1], r1);
+                    *(float4 *)(Yc + c0 + 4 * j + 2 * b) = o;
+                }
             }
             tc::fence_before();
             tc::mbar_arrive(accempty);
@@ -870,41 +927,39 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
                 failed = true;
                 break;
             }
-            const M2LWork w = work[it];
-            const int ncol = v2_ncol(w, mode);
+            const int ncol = v2_ncol(wc, mode);
             const cf *O = meta_O(slot);
             const V2Col *cols = meta_cols(slot);
-            // outputs (column cc, row r) strided by V2_ET over the item; a batch
-            // of unconditional scratch reads is issued before its atomics
-            constexpr int EB = 16;
-            int cc = 0, r = ea;
-            while (r >= P) {
-                r -= P;
-                ++cc;
-            }
-            while (cc < ncol) {
-                int bc[EB], br[EB];
-                float2 y[EB];
+            // one column per epilogue warp at a time, two in flight: lane j of a
+            // column takes rows r = lane + 32 i; the column record is warp-uniform
+            // and the scratch reads are coalesced
+            for (int c = ew; c < ncol; c += 2 * V2_EW) {
+                const int c2 = c + V2_EW;
+                const bool two = c2 < ncol;
+                float2 y[2][V2_RJ];
 #pragma unroll
-                for (int u = 0; u < EB; ++u) {
-                    bc[u] = cc;
-                    br[u] = r;
-                    y[u] = *(const float2 *)(Y + (size_t)r * 128 + 2 * min(cc, BN - 1));   // masked at use
-                    r += V2_ET;
-                    while (r >= P) {
-                        r -= P;
-                        ++cc;
-                    }
+                for (int i = 0; i < V2_RJ; ++i) {
+                    const int r = min(lane + 32 * i, P - 1);   // masked at use
+                    y[0][i] = ((const float2 *)Y)[(size_t)c * NR + r];
+                    y[1][i] = ((const float2 *)Y)[(size_t)(two ? c2 : c) * NR + r];
                 }
 #pragma unroll
-                for (int u = 0; u < EB; ++u) {
-                    if (bc[u] >= ncol) break;
-                    const V2Col &cq = cols[bc[u]];
-                    const int mh = MM[br[u]];
-                    const cf yy = O[bc[u] * MO + p + mh] * cf{y[u].x, y[u].y};
-                    // output (nu, mu) with mu = +-mh: index r or r - 2 mh
-                    atomicAdd((float2 *)(le + cq.out_base + (cq.kap < 0 ? br[u] - 2 * mh : br[u])),
-                              make_float2(yy.x, yy.y));
+                for (int h = 0; h < 2; ++h) {
+                    if (h == 1 && !two) break;
+                    const int cc = h ? c2 : c;
+                    const V2Col &cq = cols[cc];
+                    const int64_t ob = cq.out_base;
+                    const bool kneg = cq.kap < 0;
+                    const cf *Oc = O + cc * MO + p;
+#pragma unroll
+                    for (int i = 0; i < V2_RJ; ++i) {
+                        const int r = lane + 32 * i;
+                        if (r < P) {
+                            const cf yy = Oc[rm[i]] * cf{y[h][i].x, y[h][i].y};
+                            // output (nu, mu) with mu = +-mh: index r or r - 2 mh
+                            atomicAdd((float2 *)(le + ob + (kneg ? r - 2 * rm[i] : r)), make_float2(yy.x, yy.y));
+                        }
+                    }
                 }
             }
             // all epilogue threads are done with the scratch and with this meta slot:
@@ -914,7 +969,7 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
                 failed = true;
                 break;
             }
-            if (it + 2 * (int64_t)gridDim.x < nwork) fill(it + 2 * (int64_t)gridDim.x, slot);
+            if (itn < nwork) fill(wn, slot);
         }
     }
     if (failed) atomicOr(status, 4);
@@ -923,27 +978,41 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
     if (warp == 0) tc::tmem_dealloc(tbase, 512);
 }
 
+// three-piece bf16 split of a double (host and device)
+__host__ __device__ inline void v2_split3(double v, __nv_bfloat16 (&o)[V2_NPC])
+{
+    o[0] = __float2bfloat16_rn((float)v);
+    const double r1 = v - (double)__bfloat162float(o[0]);
+    o[1] = __float2bfloat16_rn((float)r1);
+    o[2] = __float2bfloat16_rn((float)(r1 - (double)__bfloat162float(o[1])));
+}
+
+// element (r, kk) of one plane of one K-step (16 real K) of a tiled image, in
+// 16-bit units: NR rows x 16 values, K-major core matrices of 8 rows x 8
+// values, the two K halves 128 B apart, 8-row groups 256 B apart
+__host__ __device__ inline size_t v2_img_off(int r, int kk)
+{
+    return (size_t)(((r >> 3) * 256 + (kk >> 3) * 128 + (r & 7) * 16 + (kk & 7) * 2) >> 1);
+}
+
 // table image of the persistent kernel: per (geometry, table) nchunk * V2_KS
-// K-steps (zero beyond P), each the TF32 hi plane then the lo plane of NR
-// rows x 8 real K in the canonical K-major layout, from the FP64 table with
-// the level scaling
-// s_t^nu s_s^n' and the degree factors (-i)^nu f_t^nu, i^n' f_s^n' applied
-// before the split
+// K-steps (zero beyond P), each V2_NPC bf16 planes of NR rows x 16 real K,
+// from the FP64 table with the level scaling s_t^nu s_s^n' and the degree
+// factors (-i)^nu f_t^nu, i^n' f_s^n' applied before the split
 __global__ void k_tile_tables(int p, int64_t g0, int64_t ng, const GeomDev *geoms, const CompDev *comps,
-                              const cd *tab64, float *img)
+                              const cd *tab64, __nv_bfloat16 *img)
 {
     const int P = (p + 1) * (p + 1);
     const V2Plan sp = v2_plan(p);
-    const int NR = (int)sp.NR;
+    const int NR = (int)sp.NR, nsub = (int)sp.nchunk * V2_KS;
     const int64_t gi = g0 + blockIdx.y;
     const int t = blockIdx.z;
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    const int nsub = (int)sp.nchunk * V2_KS;
     if (e >= nsub * NR * 8 || gi >= g0 + ng) return;
-    const int c = e / (NR * 8), rem = e % (NR * 8), r = rem >> 3, kk = rem & 7;
-    const int k = 4 * c + (kk >> 1);
+    const int c = e / (NR * 8), rem = e % (NR * 8), r = rem >> 3, i = rem & 7;   // input 8c + i
+    const int k = 8 * c + i;
     const GeomDev &g = geoms[gi];
-    double v = 0.0;
+    cd v{0.0, 0.0};
     if (r < P && k < P) {
         int nu = (int)sqrt((double)r + 0.5), n1 = (int)sqrt((double)k + 0.5);
         while ((nu + 1) * (nu + 1) <= r) ++nu;
@@ -956,15 +1025,16 @@ __global__ void k_tile_tables(int p, int64_t g0, int64_t ng, const GeomDev *geom
         const double f = pow(g.scale_t, (double)nu) * pow(g.scale_s, (double)n1) *
                          ((flip_in && (n1 & 1)) ? -1.0 : 1.0) * ((flip_out && (nu & 1)) ? -1.0 : 1.0);
         const cd a = tab64[((gi - g0) * NTAB + t) * (int64_t)P * P + (int64_t)r * P + k];
-        const cd s = ipow<double>(n1 - nu) * (f * a);   // i^n' (-i)^nu = i^(n' - nu)
-        v = (kk & 1) ? s.y : s.x;
+        v = ipow<double>(n1 - nu) * (f * a);   // i^n' (-i)^nu = i^(n' - nu)
     }
-    const float hi = tc::tf32_round((float)v);
-    const float lo = tc::tf32_round((float)(v - (double)hi));
-    const size_t base = ((size_t)(g.tab_index * NTAB + t) * nsub + c) * (size_t)(NR * 16);
-    const int off = ((r >> 3) * 256 + (kk >> 2) * 128 + (r & 7) * 16 + (kk & 3) * 4) >> 2;
-    img[base + off] = hi;
-    img[base + NR * 8 + off] = lo;
+    __nv_bfloat16 re[V2_NPC], im[V2_NPC];
+    v2_split3(v.x, re);
+    v2_split3(v.y, im);
+    __nv_bfloat16 *sub = img + ((size_t)(g.tab_index * NTAB + t) * nsub + c) * (size_t)(NR * 16 * V2_NPC);
+    for (int pc = 0; pc < V2_NPC; ++pc) {
+        sub[(size_t)pc * NR * 16 + v2_img_off(r, 2 * i)] = re[pc];
+        sub[(size_t)pc * NR * 16 + v2_img_off(r, 2 * i + 1)] = im[pc];
+    }
 }
 
 namespace {
@@ -1000,7 +1070,11 @@ cudaError_t launch_m2l_tc(int p, int64_t nwork, const M2LWork *work, const GeomD
     return cudaGetLastError();
 }
 
-bool m2l_tc2_supported(int p) { return p >= 1 && v2_plan(p).NR <= (uint32_t)V2_NR_MAX && v2_plan(p).ST >= 4; }
+bool m2l_tc2_supported(int p)
+{
+    return p >= 1 && v2_plan(p).NR <= (uint32_t)V2_NR_MAX && 2 * v2_plan(p).NR + V2_SX * V2_XW <= 512 &&
+           v2_plan(p).ST >= 4;
+}
 
 size_t m2l_tc2_image_bytes(int p, int64_t ngeom)
 {
@@ -1011,17 +1085,17 @@ size_t m2l_tc2_image_bytes(int p, int64_t ngeom)
 size_t m2l_tc2_scratch_floats(int p, int nsm) { return (size_t)nsm * 128 * v2_plan(p).NR; }
 
 void launch_tile_tables(int p, int64_t g0, int64_t ng, const GeomDev *geoms, const CompDev *comps,
-                        const cd *tab64, float *img, cudaStream_t st)
+                        const cd *tab64, void *img, cudaStream_t st)
 {
     if (ng <= 0) return;
     const V2Plan sp = v2_plan(p);
     dim3 grid((sp.nchunk * V2_KS * sp.NR * 8 + 255) / 256, (unsigned)ng, NTAB);
-    k_tile_tables<<<grid, 256, 0, st>>>(p, g0, ng, geoms, comps, tab64, img);
+    k_tile_tables<<<grid, 256, 0, st>>>(p, g0, ng, geoms, comps, tab64, (__nv_bfloat16 *)img);
 }
 
 static cudaError_t launch_tc2(int p, int mode, int64_t nwork, const M2LWork *work, const GeomDev *geoms,
-                              const CompDev *comps, const M2LPair *pairs, const cf *ephase, const int64_t *tsrc,
-                              const int64_t *tdst, const float *img, const cf *in, cf *out, float *yscr, int nsm,
+                              const M2LPair *pairs, const cf *ephase, const int64_t *tsrc,
+                              const int64_t *tdst, const void *img, const cf *in, cf *out, float *yscr, int nsm,
                               int *status, cudaStream_t st)
 {
     if (nwork <= 0) return cudaSuccess;
@@ -1030,61 +1104,53 @@ static cudaError_t launch_tc2(int p, int mode, int64_t nwork, const M2LWork *wor
     // each CTA takes all 512 tensor-memory columns: ask for more than half of
     // an SM's shared memory so that no two CTAs are resident on one SM
     const size_t smem = std::max<size_t>(v2_plan(p).total, 116 * 1024);
-    k_m2l_tc2<<<(unsigned)grid, V2_THREADS, smem, st>>>(p, mode, nwork, work, geoms, comps, pairs, ephase, tsrc,
-                                                        tdst, img, in, out, yscr, status);
+    k_m2l_tc2<<<(unsigned)grid, V2_THREADS, smem, st>>>(p, mode, nwork, work, geoms, pairs, ephase, tsrc,
+                                                        tdst, (const uint32_t *)img, in, out, yscr, status);
     return cudaGetLastError();
 }
 
 cudaError_t launch_m2l_tc2(int p, int64_t nwork, const M2LWork *work, const GeomDev *geoms,
-                           const CompDev *comps, const M2LPair *pairs, const cf *ephase, const float *img,
+                           const M2LPair *pairs, const cf *ephase, const void *img,
                            const cf *me, cf *le, float *yscr, int nsm, int *status, cudaStream_t st)
 {
-    return launch_tc2(p, 0, nwork, work, geoms, comps, pairs, ephase, nullptr, nullptr, img, me, le, yscr, nsm,
+    return launch_tc2(p, 0, nwork, work, geoms, pairs, ephase, nullptr, nullptr, img, me, le, yscr, nsm,
                       status, st);
 }
 
 cudaError_t launch_trans_tc2(int p, int64_t nwork, const M2LWork *work, const int64_t *tsrc,
-                             const int64_t *tdst, const float *img, const cf *in, cf *out, float *yscr, int nsm,
+                             const int64_t *tdst, const void *img, const cf *in, cf *out, float *yscr, int nsm,
                              int *status, cudaStream_t st)
 {
-    return launch_tc2(p, 1, nwork, work, nullptr, nullptr, nullptr, nullptr, tsrc, tdst, img, in, out, yscr, nsm,
+    return launch_tc2(p, 1, nwork, work, nullptr, nullptr, nullptr, tsrc, tdst, img, in, out, yscr, nsm,
                       status, st);
 }
 
-size_t tc2_matrix_floats(int p)
+size_t tc2_matrix_bytes(int p)
 {
     const V2Plan sp = v2_plan(p);
-    return (size_t)sp.nchunk * sp.CB / sizeof(float);
+    return (size_t)sp.nchunk * sp.CB;
 }
 
-// TF32 rounding on the host: to nearest, ties away from zero (as cvt.rna.tf32.f32)
-static float tf32_rna_host(float x)
-{
-    uint32_t u;
-    std::memcpy(&u, &x, 4);
-    u = (u + 0x1000u) & 0xFFFFE000u;
-    float y;
-    std::memcpy(&y, &u, 4);
-    return y;
-}
-
-void tile_matrix_tc2(int p, const cd *M, float *img)
+void tile_matrix_tc2(int p, const cd *M, void *img_)
 {
     const int P = (p + 1) * (p + 1);
     const V2Plan sp = v2_plan(p);
     const int NR = (int)sp.NR, nsub = (int)sp.nchunk * V2_KS;
+    __nv_bfloat16 *img = (__nv_bfloat16 *)img_;
     for (int c = 0; c < nsub; ++c)
         for (int r = 0; r < NR; ++r)
-            for (int kk = 0; kk < 8; ++kk) {
-                const int k = 4 * c + (kk >> 1);
-                double v = 0.0;
-                if (r < P && k < P) v = (kk & 1) ? M[(size_t)r * P + k].y : M[(size_t)r * P + k].x;
-                const float hi = tf32_rna_host((float)v);
-                const float lo = tf32_rna_host((float)(v - (double)hi));
-                const size_t base = (size_t)c * NR * 16;
-                const int off = ((r >> 3) * 256 + (kk >> 2) * 128 + (r & 7) * 16 + (kk & 3) * 4) >> 2;
-                img[base + off] = hi;
-                img[base + NR * 8 + off] = lo;
+            for (int i = 0; i < 8; ++i) {
+                const int k = 8 * c + i;
+                cd v{0.0, 0.0};
+                if (r < P && k < P) v = M[(size_t)r * P + k];
+                __nv_bfloat16 re[V2_NPC], im[V2_NPC];
+                v2_split3(v.x, re);
+                v2_split3(v.y, im);
+                __nv_bfloat16 *sub = img + (size_t)c * NR * 16 * V2_NPC;
+                for (int pc = 0; pc < V2_NPC; ++pc) {
+                    sub[(size_t)pc * NR * 16 + v2_img_off(r, 2 * i)] = re[pc];
+                    sub[(size_t)pc * NR * 16 + v2_img_off(r, 2 * i + 1)] = im[pc];
+                }
             }
 }
 

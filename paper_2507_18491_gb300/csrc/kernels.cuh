@@ -54,7 +54,8 @@ struct GemmWork {       // M2M / L2L: pairs [pair0, pair0 + npair) of one transl
 };
 
 struct M2LWork {        // one M2L table applied to a chunk of pairs of one geometry
-    int geom, t, npair, pad;
+    int geom, t, npair;
+    int flags;          // bit 0: odd input degrees change sign, bit 1: odd output degrees
     int64_t pair0;
 };
 
@@ -100,27 +101,27 @@ cudaError_t configure_m2l_tc();
 cudaError_t launch_m2l_tc(int p, int64_t nwork, const M2LWork *work, const GeomDev *geoms,
                           const CompDev *comps, const M2LPair *pairs, const cf *tab, const cf *me,
                           cf *le, int *status, cudaStream_t st);
-// persistent warp-specialised variant (p <= 13) on a pre-tiled TF32 hi/lo
-// table image written by launch_tile_tables from the FP64 tables; ephase
-// holds e^{i d phi} of every pair, d = -(p+2)..p+2 ([npair][2p+5], FP32 from
-// FP64); yscr holds m2l_tc2_scratch_floats(p, nsm) floats, nsm = CTAs of the
-// launch (the SM count)
+// persistent warp-specialised variant (p <= 12) on a pre-tiled image of the
+// tables in three bf16 pieces (launch_tile_tables from the FP64 tables);
+// ephase holds e^{i d phi} of every pair, d = -(p+2)..p+2 ([npair][2p+5],
+// FP32 from FP64); yscr holds m2l_tc2_scratch_floats(p, nsm) floats, nsm =
+// CTAs of the launch (the SM count)
 bool m2l_tc2_supported(int p);
 size_t m2l_tc2_image_bytes(int p, int64_t ngeom);
 size_t m2l_tc2_scratch_floats(int p, int nsm);
 void launch_tile_tables(int p, int64_t g0, int64_t ng, const GeomDev *geoms, const CompDev *comps,
-                        const cd *tab64, float *img, cudaStream_t st);
+                        const cd *tab64, void *img, cudaStream_t st);
 cudaError_t launch_m2l_tc2(int p, int64_t nwork, const M2LWork *work, const GeomDev *geoms,
-                           const CompDev *comps, const M2LPair *pairs, const cf *ephase, const float *img,
+                           const M2LPair *pairs, const cf *ephase, const void *img,
                            const cf *me, cf *le, float *yscr, int nsm, int *status, cudaStream_t st);
 // M2M or L2L on the same kernel: items M2LWork{geom = translation group, t = 0,
 // npair, pair0} over pairs (tsrc[q], tdst[q]), 3 helical columns each; img holds
-// one tiled matrix per group (tile_matrix_tc2, tc2_matrix_floats(p) floats each)
+// one tiled matrix per group (tile_matrix_tc2, tc2_matrix_bytes(p) each)
 cudaError_t launch_trans_tc2(int p, int64_t nwork, const M2LWork *work, const int64_t *tsrc,
-                             const int64_t *tdst, const float *img, const cf *in, cf *out, float *yscr, int nsm,
+                             const int64_t *tdst, const void *img, const cf *in, cf *out, float *yscr, int nsm,
                              int *status, cudaStream_t st);
-size_t tc2_matrix_floats(int p);
-void tile_matrix_tc2(int p, const cd *M, float *img);   // host: P x P row-major (row = output index)
+size_t tc2_matrix_bytes(int p);
+void tile_matrix_tc2(int p, const cd *M, void *img);   // host: P x P row-major (row = output index)
 template <typename T>
 void launch_scale_tables(int p, int64_t g0, int64_t ng, const GeomDev *geoms, const cd *tab64,
                          cx<T> *tab, cudaStream_t st);

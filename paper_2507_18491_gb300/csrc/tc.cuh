@@ -34,6 +34,24 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N, bool negA)
            ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// Instruction descriptor of kind::f16 with bf16 A and B (K-major), D f32, shape M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// MMA kind::f16 (K = 16, fp16 or bf16 per the instruction descriptor) with the
+// A operand in tensor memory (M lanes x 8 columns, two 16-bit values per
+// column, even K in the low half) and B in shared memory
+__device__ __forceinline__ void mma_f16_ta(uint32_t dtmem, uint32_t atmem, uint64_t db, uint32_t idesc,
+                                           uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(dtmem),
+        "r"(atmem), "l"(db), "r"(idesc), "r"(accumulate));
+}
+
 __device__ __forceinline__ void tmem_alloc(uint32_t *dst_smem, uint32_t ncols)
 {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -132,6 +150,17 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t r[8])
                  "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
                  : "memory");
 }
+// 32 lanes x 16 consecutive 32-bit columns from registers into tensor memory
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t r[16])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+            taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+        "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
+
 // 32 lanes x 32 consecutive 32-bit columns from registers into tensor memory
 __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t r[32])
 {
