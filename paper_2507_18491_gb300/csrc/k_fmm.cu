@@ -48,155 +48,316 @@ void launch_scatter_out(int64_t N, const int64_t *perm, const cd *phih, cd *Phi,
 }
 
 // --------------------------------------------------------------- P2M, L2P
-// basis b_nm(r) = j_n(k |r|) Y_n^m(r^) / s^n with Y_n^m = P^_n^|m| e^{i m phi}
-// (times (-1)^m for m < 0) and the leaf scale s = |k| S_leaf; P2M uses
-// 4 pi conj(Y) (eq. mecoeff).  Computed in double, stored as T.
-// j_n(z) / w^n, n = 0..p, for |z| < 1.5 by the power series
-//   j_n(z) = z^n / (2n+1)!! sum_k (-z^2/2)^k / (k! (2n+3)(2n+5)...(2n+2k+1)),
-// carried out in T with zeta = z/w so that no power of z over- or underflows.
-template <typename T>
-static __device__ inline void sph_bessel_scaled_series(cx<T> z, cx<T> zeta, int p, cx<T> *j)
-{
-    cx<T> q = T(-0.5) * (z * z);
-    cx<T> zn{T(1), T(0)};
-    T df = T(1);   // (2n+1)!!
-    for (int n = 0; n <= p; ++n) {
-        if (n > 0) {
-            zn = zn * zeta;
-            df *= T(2 * n + 1);
-        }
-        cx<T> term{T(1), T(0)}, sum{T(1), T(0)};
-        for (int k = 1; k <= 14; ++k) {
-            term = term * q * (T(1) / (T(k) * T(2 * n + 2 * k + 1)));
-            sum += term;
-            if (abs2(term) < T(1e-18) * abs2(sum)) break;
-        }
-        j[n] = (zn * sum) * (T(1) / df);
-    }
-}
-
-// basis b_nm(r) = scale * j_n(k |r|) Y_n^m(r^) / s^n with Y_n^m = P^_n^|m| e^{i m phi}
+// ------------------------------------------------- basis of a chunk of points
+// b_nm(r) = scale * j_n(k |r|) Y_n^m(r^) / s^n with Y_n^m = P^_n^|m| e^{i m phi}
 // (times (-1)^m for m < 0), s = |k| S_leaf; P2M uses scale = 4 pi and conj(Y)
 // (eq. mecoeff).  FP64 form in double; mixed form in float when |k r| < 1.5.
-// visit(index n^2+n+m, b_nm) is called once per coefficient.
-template <typename T, typename Visit>
-static __device__ inline void point_basis_visit(int p, cd k, double dx, double dy, double dz,
-                                                bool conjugate, double scale, double inv_s,
-                                                Visit visit)
+// The whole CTA builds the basis of up to CH points at once: one thread per
+// point for the radial factors j_n (and the angle seeds), then one thread per
+// (point, pair of orders m, p - m) for the normalised Legendre recurrence in n,
+// whose coefficients come from a per-CTA table.
+constexpr int SER_K = 14;   // terms of the power series of j_n
+
+template <typename T>
+struct LegTab {
+    T *a, *b;   // [n(n+1)/2 + m]: P_n^m = a (x P_{n-1}^m - b P_{n-2}^m), n >= m + 2
+    T *d;       // [m]: P_{m+1}^m = d x P_m^m
+    T *c;       // [m]: P_m^m = -c s P_{m-1}^m, c = sqrt((2m+1)/(2m)), c[0] = 1/sqrt(4 pi)
+    T *sk;      // [n][k-1]: 1 / (k (2n+2k+1)), ratio of consecutive series terms of j_n
+    T *idf;     // [n]: 1 / (2n+1)!!
+};
+
+template <typename T>
+__host__ __device__ constexpr size_t legtab_elems(int p)
 {
-    double r = sqrt(dx * dx + dy * dy + dz * dz);
-    double rxy = sqrt(dx * dx + dy * dy);
-    double ct = r > 0 ? dz / r : 1.0, st = r > 0 ? rxy / r : 0.0;
-    cx<T> jn[LMF_PMAX + 1];
-    cd kr = k * r;
+    return (size_t)(p + 1) * (p + 2) + 3 * (size_t)(p + 1) + (size_t)(p + 1) * SER_K;
+}
+
+template <typename T>
+__device__ inline LegTab<T> legtab_fill(int p, T *mem)
+{
+    const int NT = (p + 1) * (p + 2) / 2;
+    LegTab<T> L{mem, mem + NT, mem + 2 * NT, mem + 2 * NT + p + 1, mem + 2 * NT + 2 * (p + 1),
+                mem + 2 * NT + 2 * (p + 1) + (p + 1) * SER_K};
+    for (int e = threadIdx.x; e < NT; e += blockDim.x) {
+        int n = (int)sqrtf(2.0f * e + 0.25f);
+        while ((n + 1) * (n + 2) / 2 <= e) ++n;
+        while (n * (n + 1) / 2 > e) --n;
+        const int m = e - n * (n + 1) / 2;
+        T av = T(0), bv = T(0);
+        if (n >= m + 2) {
+            av = sqrt(T(4 * n * n - 1) / T(n * n - m * m));
+            bv = sqrt(T((n - 1) * (n - 1) - m * m) / T(4 * (n - 1) * (n - 1) - 1));
+        }
+        L.a[e] = av;
+        L.b[e] = bv;
+    }
+    for (int m = threadIdx.x; m <= p; m += blockDim.x) {
+        L.d[m] = sqrt(T(2 * m + 3));
+        L.c[m] = m == 0 ? T(0.28209479177387814347) : sqrt(T(2 * m + 1) / T(2 * m));
+        T df = T(1);
+        for (int i = 1; i <= m; ++i) df *= T(2 * i + 1);
+        L.idf[m] = T(1) / df;
+    }
+    for (int e = threadIdx.x; e < (p + 1) * SER_K; e += blockDim.x) {
+        const int n = e / SER_K, k = e - n * SER_K + 1;
+        L.sk[e] = T(1) / (T(k) * T(2 * n + 2 * k + 1));
+    }
+    return L;
+}
+
+// angle seeds of point j, geo[j] = (cos theta, sin theta, Re e^{i phi},
+// Im e^{i phi}) (conjugated for P2M), and its radial factors jr[j][n]
+// (scale / s^n included) when they come from the FP64 recurrence; otherwise
+// (mixed form, |k r| < 1.5) kz[j] = (k r, k r / s) for the power series,
+// evaluated one degree per thread by series_degree
+template <typename T>
+__device__ inline void point_seed(int p, cd k, double dx, double dy, double dz, bool conjugate,
+                                  double scale, double inv_s, cx<T> *jr, T *geo, cx<T> *kz)
+{
+    const double r = sqrt(dx * dx + dy * dy + dz * dz);
+    const double rxy = sqrt(dx * dx + dy * dy);
+    geo[0] = (T)(r > 0 ? dz / r : 1.0);
+    geo[1] = (T)(r > 0 ? rxy / r : 0.0);
+    geo[2] = (T)(rxy > 0 ? dx / rxy : 1.0);
+    geo[3] = (T)(rxy > 0 ? (conjugate ? -dy : dy) / rxy : 0.0);
+    const cd kr = k * r;
     if (sizeof(T) == 4 && cabsd(kr) < 1.5) {
-        cd zeta = (r * inv_s) * k;
-        sph_bessel_scaled_series<T>(cx<T>{(T)kr.x, (T)kr.y}, cx<T>{(T)zeta.x, (T)zeta.y}, p, jn);
-        for (int n = 0; n <= p; ++n) jn[n] = (T)scale * jn[n];
+        const cd zeta = (r * inv_s) * k;
+        kz[0] = cx<T>{(T)kr.x, (T)kr.y};
+        kz[1] = cx<T>{(T)zeta.x, (T)zeta.y};
     } else {
+        kz[0] = cx<T>{T(-1), T(0)};   // marker: jr already set
         cd jd[LMF_PMAX + 1];
         sph_bessel_seq(kr, p, jd);
         double sp = scale;
         for (int n = 0; n <= p; ++n) {
-            jn[n] = cx<T>{(T)(sp * jd[n].x), (T)(sp * jd[n].y)};
+            jr[n] = cx<T>{(T)(sp * jd[n].x), (T)(sp * jd[n].y)};
             sp *= inv_s;
         }
     }
-    T Pl[(LMF_PMAX + 1) * (LMF_PMAX + 2) / 2];
-    legendre_norm<T>(p, (T)ct, (T)st, Pl);
-    cx<T> e1 = rxy > 0 ? cx<T>{(T)(dx / rxy), (T)(dy / rxy)} : cx<T>{T(1), T(0)};
-    if (conjugate) e1 = conj(e1);
-    cx<T> em{T(1), T(0)};
-    for (int m = 0; m <= p; ++m) {
-        cx<T> emc = conj(em);
-        T sg = (m & 1) ? T(-1) : T(1);
-        for (int n = m; n <= p; ++n) {
-            cx<T> jv = Pl[(n * (n + 1)) / 2 + m] * jn[n];
-            visit(n * n + n + m, jv * em);
-            if (m > 0) visit(n * n + n - m, sg * (jv * emc));
-        }
-        em = em * e1;
+}
+
+// scale * j_n(z) / w^n, z = k r, for |z| < 1.5 by the power series
+//   j_n(z) = z^n / (2n+1)!! sum_k (-z^2/2)^k / (k! (2n+3)(2n+5)...(2n+2k+1)),
+// carried out in T with zeta = z / w so that no power of z over- or underflows
+template <typename T>
+__device__ inline cx<T> series_degree(int n, cx<T> z, cx<T> zeta, T scale, const LegTab<T> &L)
+{
+    const cx<T> q = T(-0.5) * (z * z);
+    cx<T> zn{T(1), T(0)};
+    for (int i = 0; i < n; ++i) zn = zn * zeta;
+    cx<T> term{T(1), T(0)}, sum{T(1), T(0)};
+    for (int k = 1; k <= SER_K; ++k) {
+        term = term * q * L.sk[n * SER_K + k - 1];
+        sum += term;
+        if (abs2(term) < T(1e-18) * abs2(sum)) break;
+    }
+    return scale * ((zn * sum) * L.idf[n]);
+}
+
+// column m of point j: b_{n, +-m} for n = m..p into bj[n^2 + n +- m], from
+// P_m^m (pmm) and e^{i m phi} (em) already advanced to order m
+template <typename T>
+__device__ inline void basis_column(int p, int m, T x, T pmm, cx<T> em, const cx<T> *jr,
+                                    const LegTab<T> &L, cx<T> *bj)
+{
+    const cx<T> emc = conj(em);
+    const T sg = (m & 1) ? T(-1) : T(1);
+    auto put = [&](int n, T pl) {
+        const cx<T> jv = pl * jr[n];
+        bj[n * n + n + m] = jv * em;
+        if (m > 0) bj[n * n + n - m] = sg * (jv * emc);
+    };
+    put(m, pmm);
+    if (m == p) return;
+    T p0 = pmm, p1 = L.d[m] * x * pmm;
+    put(m + 1, p1);
+    for (int n = m + 2; n <= p; ++n) {
+        const int e = n * (n + 1) / 2 + m;
+        const T p2 = L.a[e] * (x * p1 - L.b[e] * p0);
+        put(n, p2);
+        p0 = p1;
+        p1 = p2;
     }
 }
 
+// basis of points t0 .. t0+np-1 (np <= CH) into bas[j * P + index]; the caller
+// synchronises before reading bas
 template <typename T>
-static __device__ inline void point_basis(int p, cd k, double dx, double dy, double dz,
-                                          bool conjugate, double scale, double inv_s, cx<T> *out)
+__device__ inline void chunk_basis(int p, cd k, const double *xyz, const double *ctr, int64_t t0, int np,
+                                   bool conjugate, double scale, double inv_s, const LegTab<T> &L,
+                                   cx<T> *jr, T *geo, cx<T> *kz, cx<T> *bas)
 {
-    point_basis_visit<T>(p, k, dx, dy, dz, conjugate, scale, inv_s,
-                         [&](int i, cx<T> v) { out[i] = v; });
+    const int P = (p + 1) * (p + 1);
+    for (int j = threadIdx.x; j < np; j += blockDim.x) {
+        const int64_t t = t0 + j;
+        point_seed<T>(p, k, xyz[3 * t] - ctr[0], xyz[3 * t + 1] - ctr[1], xyz[3 * t + 2] - ctr[2],
+                      conjugate, scale, inv_s, jr + j * (p + 1), geo + 4 * j, kz + 2 * j);
+    }
+    __syncthreads();
+    if (sizeof(T) == 4) {
+        for (int task = threadIdx.x; task < np * (p + 1); task += blockDim.x) {
+            const int j = task / (p + 1), n = task - j * (p + 1);
+            const cx<T> z = kz[2 * j];
+            if (z.x == T(-1) && z.y == T(0)) continue;   // recurrence path: jr is set
+            jr[task] = series_degree<T>(n, z, kz[2 * j + 1], (T)scale, L);
+        }
+        __syncthreads();
+    }
+    // orders m and p - m share a task: p + 2 terms of the recurrence per task
+    const int nt = p / 2 + 1;
+    for (int task = threadIdx.x; task < np * nt; task += blockDim.x) {
+        const int j = task / nt, m1 = task - j * nt, m2 = p - m1;
+        const T x = geo[4 * j], sv = geo[4 * j + 1];
+        const cx<T> e1{geo[4 * j + 2], geo[4 * j + 3]};
+        T pmm = L.c[0];
+        cx<T> em{T(1), T(0)};
+        for (int m = 1; m <= m1; ++m) {
+            pmm = -pmm * sv * L.c[m];
+            em = em * e1;
+        }
+        basis_column<T>(p, m1, x, pmm, em, jr + j * (p + 1), L, bas + (size_t)j * P);
+        if (m2 != m1) {
+            for (int m = m1 + 1; m <= m2; ++m) {
+                pmm = -pmm * sv * L.c[m];
+                em = em * e1;
+            }
+            basis_column<T>(p, m2, x, pmm, em, jr + j * (p + 1), L, bas + (size_t)j * P);
+        }
+    }
 }
 
+// shared-memory plan of the P2M / L2P kernels: CH points per chunk
 template <typename T>
-__global__ void k_p2m(int p, const int64_t *leaves, const BoxDev *boxes, const double *xyz,
-                      const cd *qh, MediumDev M, LayerScale ls, cx<T> *me)
+struct LeafSmem {
+    int CH;
+    size_t leg, geo, kz, jr, bas, extra, total;   // byte offsets, extra: hq (P2M) or L (L2P)
+};
+
+template <typename T>
+__host__ __device__ inline LeafSmem<T> leaf_smem(int p, bool l2p, size_t cap)
 {
-    extern __shared__ unsigned char smraw[];
+    const size_t P = (size_t)(p + 1) * (p + 1);
+    LeafSmem<T> s{};
+    for (s.CH = 32; s.CH >= 4; s.CH /= 2) {
+        s.leg = 0;
+        s.geo = (legtab_elems<T>(p) * sizeof(T) + 15) & ~(size_t)15;
+        s.kz = s.geo + ((4 * s.CH * sizeof(T) + 15) & ~(size_t)15);
+        s.jr = s.kz + 2 * s.CH * sizeof(cx<T>);
+        s.bas = s.jr + s.CH * (p + 1) * sizeof(cx<T>);
+        s.extra = s.bas + s.CH * P * sizeof(cx<T>);
+        s.total = s.extra + (l2p ? 3 * P : 3 * (size_t)s.CH) * sizeof(cx<T>);
+        if (s.total <= cap) break;
+    }
+    return s;
+}
+
+constexpr size_t LEAF_SMEM_CAP = 200 * 1024;   // dynamic shared memory granted to these kernels
+
+// One CTA per leaf: chunks of CH points are turned into their basis by the
+// whole CTA, then each thread accumulates its multipole coefficients over the
+// chunk's points.
+template <typename T>
+__global__ void __launch_bounds__(256) k_p2m(int p, int CH, const int64_t *leaves, const BoxDev *boxes,
+                                             const double *xyz, const cd *qh, MediumDev M, LayerScale ls,
+                                             cx<T> *me)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
     const int P = (p + 1) * (p + 1);
-    const int CH = 32;
-    cx<T> *bas = (cx<T> *)smraw;    // [CH][P]
-    cx<T> *hq = bas + CH * P;       // [CH][3]
-    int64_t bi = leaves[blockIdx.x];
-    BoxDev b = boxes[bi];
-    cd k = M.k[b.layer];
+    const LeafSmem<T> sp = leaf_smem<T>(p, false, LEAF_SMEM_CAP);
+    const LegTab<T> L = legtab_fill<T>(p, (T *)(smraw + sp.leg));
+    T *geo = (T *)(smraw + sp.geo);
+    cx<T> *kz = (cx<T> *)(smraw + sp.kz);
+    cx<T> *jr = (cx<T> *)(smraw + sp.jr);
+    cx<T> *bas = (cx<T> *)(smraw + sp.bas);
+    cx<T> *hq = (cx<T> *)(smraw + sp.extra);   // [CH][3]
+    const int64_t bi = leaves[blockIdx.x];
+    const BoxDev b = boxes[bi];
+    const cd k = M.k[b.layer];
     const double inv_s = 1.0 / ls.s[b.layer];
     const int NO = 3 * P;
-    const int PER = (NO + blockDim.x - 1) / blockDim.x;
-    cx<T> acc[8];
-    for (int i = 0; i < 8; ++i) acc[i] = cx<T>{T(0), T(0)};
+    constexpr int PERMAX = (3 * (LMF_PMAX + 1) * (LMF_PMAX + 1) + 255) / 256;
+    cx<T> acc[PERMAX];
+#pragma unroll
+    for (int i = 0; i < PERMAX; ++i) acc[i] = cx<T>{T(0), T(0)};
     for (int64_t c0 = b.p0; c0 < b.p1; c0 += CH) {
-        int np = (int)min((int64_t)CH, b.p1 - c0);
-        if (threadIdx.x < np) {
-            int j = threadIdx.x;
-            int64_t t = c0 + j;
-            point_basis<T>(p, k, xyz[3 * t] - b.c[0], xyz[3 * t + 1] - b.c[1],
-                           xyz[3 * t + 2] - b.c[2], true, 4.0 * LMF_PI, inv_s, bas + j * P);
-            for (int v = 0; v < 3; ++v) hq[3 * j + v] = cx<T>{(T)qh[3 * t + v].x, (T)qh[3 * t + v].y};
-        }
+        const int np = (int)min((int64_t)CH, b.p1 - c0);
+        for (int e = threadIdx.x; e < 3 * np; e += blockDim.x)
+            hq[e] = cx<T>{(T)qh[3 * c0 + e].x, (T)qh[3 * c0 + e].y};
+        chunk_basis<T>(p, k, xyz, b.c, c0, np, true, 4.0 * LMF_PI, inv_s, L, jr, geo, kz, bas);
         __syncthreads();
-        for (int i = 0; i < PER; ++i) {
-            int o = threadIdx.x + i * blockDim.x;
-            if (o >= NO) break;
-            int v = o / P, nm = o % P;
-            cx<T> a = acc[i];
-            for (int j = 0; j < np; ++j) a += hq[3 * j + v] * bas[j * P + nm];
-            acc[i] = a;
+#pragma unroll
+        for (int i = 0; i < PERMAX; ++i) {
+            const int o = threadIdx.x + i * blockDim.x;
+            if (o < NO) {
+                const int v = o / P, nm = o - v * P;
+                cx<T> a = acc[i];
+                for (int j = 0; j < np; ++j) a += hq[3 * j + v] * bas[j * P + nm];
+                acc[i] = a;
+            }
         }
         __syncthreads();
     }
-    for (int i = 0; i < PER; ++i) {
-        int o = threadIdx.x + i * blockDim.x;
+#pragma unroll
+    for (int i = 0; i < PERMAX; ++i) {
+        const int o = threadIdx.x + i * blockDim.x;
         if (o < NO) me[bi * NO + o] = acc[i];
     }
 }
 
-// One CTA per leaf, one thread per target point: the basis is generated
-// coefficient by coefficient and contracted at once with the three local
+// One CTA per leaf: chunks of CH target points are turned into their basis by
+// the whole CTA, then one warp per point contracts it with the three local
 // expansions held in shared memory.
 template <typename T>
-__global__ void k_l2p(int p, const int64_t *leaves, const BoxDev *boxes, const double *xyz,
-                      const cx<T> *le, MediumDev M, LayerScale ls, cd *ph)
+__global__ void __launch_bounds__(256) k_l2p(int p, int CH, const int64_t *leaves, const BoxDev *boxes,
+                                             const double *xyz, const cx<T> *le, MediumDev M, LayerScale ls,
+                                             cd *ph)
 {
-    extern __shared__ unsigned char smraw[];
+    extern __shared__ __align__(16) unsigned char smraw[];
     const int P = (p + 1) * (p + 1);
-    cx<T> *L = (cx<T> *)smraw;          // [3][P]
-    int64_t bi = leaves[blockIdx.x];
-    BoxDev b = boxes[bi];
-    for (int e = threadIdx.x; e < 3 * P; e += blockDim.x) L[e] = le[bi * 3 * P + e];
-    __syncthreads();
-    cd k = M.k[b.layer];
+    const LeafSmem<T> sp = leaf_smem<T>(p, true, LEAF_SMEM_CAP);
+    const LegTab<T> L = legtab_fill<T>(p, (T *)(smraw + sp.leg));
+    T *geo = (T *)(smraw + sp.geo);
+    cx<T> *kz = (cx<T> *)(smraw + sp.kz);
+    cx<T> *jr = (cx<T> *)(smraw + sp.jr);
+    cx<T> *bas = (cx<T> *)(smraw + sp.bas);
+    cx<T> *Lc = (cx<T> *)(smraw + sp.extra);   // [3][P]
+    const int64_t bi = leaves[blockIdx.x];
+    const BoxDev b = boxes[bi];
+    for (int e = threadIdx.x; e < 3 * P; e += blockDim.x) Lc[e] = le[bi * 3 * P + e];
+    const cd k = M.k[b.layer];
     const double inv_s = 1.0 / ls.s[b.layer];
-    for (int64_t t = b.p0 + threadIdx.x; t < b.p1; t += blockDim.x) {
-        cx<T> A{T(0), T(0)}, B{T(0), T(0)}, C{T(0), T(0)};
-        point_basis_visit<T>(p, k, xyz[3 * t] - b.c[0], xyz[3 * t + 1] - b.c[1],
-                             xyz[3 * t + 2] - b.c[2], false, 1.0, inv_s, [&](int i, cx<T> bv) {
-                                 A += L[i] * bv;
-                                 B += L[P + i] * bv;
-                                 C += L[2 * P + i] * bv;
-                             });
-        ph[3 * t] = cd{(double)A.x, (double)A.y};
-        ph[3 * t + 1] = cd{(double)B.x, (double)B.y};
-        ph[3 * t + 2] = cd{(double)C.x, (double)C.y};
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+    for (int64_t c0 = b.p0; c0 < b.p1; c0 += CH) {
+        const int np = (int)min((int64_t)CH, b.p1 - c0);
+        chunk_basis<T>(p, k, xyz, b.c, c0, np, false, 1.0, inv_s, L, jr, geo, kz, bas);
+        __syncthreads();
+        for (int j = warp; j < np; j += nwarp) {
+            cx<T> A{T(0), T(0)}, B{T(0), T(0)}, C{T(0), T(0)};
+            for (int i = lane; i < P; i += 32) {
+                const cx<T> bv = bas[j * P + i];
+                A += Lc[i] * bv;
+                B += Lc[P + i] * bv;
+                C += Lc[2 * P + i] * bv;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                A.x += __shfl_xor_sync(0xffffffffu, A.x, o);
+                A.y += __shfl_xor_sync(0xffffffffu, A.y, o);
+                B.x += __shfl_xor_sync(0xffffffffu, B.x, o);
+                B.y += __shfl_xor_sync(0xffffffffu, B.y, o);
+                C.x += __shfl_xor_sync(0xffffffffu, C.x, o);
+                C.y += __shfl_xor_sync(0xffffffffu, C.y, o);
+            }
+            if (lane == 0) {
+                const int64_t t = c0 + j;
+                ph[3 * t] = cd{(double)A.x, (double)A.y};
+                ph[3 * t + 1] = cd{(double)B.x, (double)B.y};
+                ph[3 * t + 2] = cd{(double)C.x, (double)C.y};
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -206,10 +367,8 @@ void launch_p2m(int p, int64_t nleaf, const int64_t *leaves, const BoxDev *boxes
                 cx<T> *me, cudaStream_t st)
 {
     if (nleaf <= 0) return;
-    const int P = (p + 1) * (p + 1);
-    size_t sm = (size_t)(32 * P + 32 * 3) * sizeof(cx<T>);
-    int thr = 3 * P <= 8 * 128 ? 128 : 256;
-    k_p2m<T><<<(unsigned)nleaf, thr, sm, st>>>(p, leaves, boxes, xyz, qh, M, ls, me);
+    const LeafSmem<T> sp = leaf_smem<T>(p, false, LEAF_SMEM_CAP);
+    k_p2m<T><<<(unsigned)nleaf, 256, sp.total, st>>>(p, sp.CH, leaves, boxes, xyz, qh, M, ls, me);
 }
 
 template <typename T>
@@ -218,10 +377,8 @@ void launch_l2p(int p, int64_t nleaf, const int64_t *leaves, const BoxDev *boxes
                 cd *phih, cudaStream_t st)
 {
     if (nleaf <= 0) return;
-    const int P = (p + 1) * (p + 1);
-    const int thr = 64;
-    size_t sm = (size_t)(3 * P) * sizeof(cx<T>);
-    k_l2p<T><<<(unsigned)nleaf, thr, sm, st>>>(p, leaves, boxes, xyz, le, M, ls, phih);
+    const LeafSmem<T> sp = leaf_smem<T>(p, true, LEAF_SMEM_CAP);
+    k_l2p<T><<<(unsigned)nleaf, 256, sp.total, st>>>(p, sp.CH, leaves, boxes, xyz, le, M, ls, phih);
 }
 
 template void launch_p2m<float>(int, int64_t, const int64_t *, const BoxDev *, const double *,
@@ -493,7 +650,7 @@ void launch_s2t_apply(int64_t nnear, const NearPair *near, const BoxDev *boxes,
 namespace lmf {
 cudaError_t configure_fmm_kernels()
 {
-    const int big = 200 * 1024;
+    const int big = (int)LEAF_SMEM_CAP;
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_p2m<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_p2m<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;

@@ -25,40 +25,79 @@ template <> struct TileCfg<float> { static constexpr int TM = 4, TN = 4, BK = 16
 template <> struct TileCfg<double> { static constexpr int TM = 4, TN = 2, BK = 16; };
 
 // Y(P x BN) = A(P x P, row-major, global) X(P x BN, shared); 256 threads as a
-// 16 x 16 grid, each owning TM rows x TN columns; A streams through shared
-// memory in BM x BK tiles.  store(r, c, y) for r < P, c < ncol.
+// 16 x 16 grid, each owning TM rows x TN columns.  A streams through two
+// shared-memory tiles of BK x BM (k-major, rows padded to BMP so that the
+// transposing stores spread over banks and every thread's TM rows stay 16-byte
+// aligned); the next tile is fetched into registers while the current one is
+// multiplied.  The TM rows and TN columns of a thread are read with 16-byte
+// loads.  store(r, c, y) for r < P, c < ncol.
+template <typename T>
+struct GemmTile {
+    static constexpr int TM = TileCfg<T>::TM, TN = TileCfg<T>::TN, BK = TileCfg<T>::BK;
+    static constexpr int BM = 16 * TM, BN = 16 * TN, BMP = BM + 2;
+    static constexpr int LPT = BM * BK / 256;   // tile elements loaded per thread
+};
+
+template <typename T, int N>
+__device__ __forceinline__ void lds_vec(const cx<T> *src, cx<T> (&dst)[N])
+{
+    static_assert((N * sizeof(cx<T>)) % 16 == 0, "whole 16-byte words");
+    const float4 *s4 = (const float4 *)src;
+#pragma unroll
+    for (int i = 0; i < (int)(N * sizeof(cx<T>) / 16); ++i) {
+        const float4 v = s4[i];
+        memcpy((char *)dst + 16 * i, &v, 16);
+    }
+}
+
 template <typename T, typename Store>
 __device__ __forceinline__ void tiled_gemm(int P, const cx<T> *__restrict__ A, const cx<T> *X,
                                            cx<T> *As, int ncol, Store store)
 {
-    constexpr int TM = TileCfg<T>::TM, TN = TileCfg<T>::TN, BK = TileCfg<T>::BK;
-    constexpr int BM = 16 * TM, BN = 16 * TN;
+    using G = GemmTile<T>;
+    constexpr int TM = G::TM, TN = G::TN, BK = G::BK, BM = G::BM, BN = G::BN, BMP = G::BMP;
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const int nk = (P + BK - 1) / BK;
+    auto fetch = [&](int r0, int k0, cx<T> (&v)[G::LPT]) {
+#pragma unroll
+        for (int u = 0; u < G::LPT; ++u) {
+            const int e = threadIdx.x + 256 * u, r = e / BK, kk = e % BK;
+            const int gr = r0 + r, gk = k0 + kk;
+            v[u] = (gr < P && gk < P) ? A[(int64_t)gr * P + gk] : cx<T>{T(0), T(0)};
+        }
+    };
+    auto put = [&](int buf, const cx<T> (&v)[G::LPT]) {
+#pragma unroll
+        for (int u = 0; u < G::LPT; ++u) {
+            const int e = threadIdx.x + 256 * u, r = e / BK, kk = e % BK;
+            As[buf * BK * BMP + kk * BMP + r] = v[u];
+        }
+    };
     for (int r0 = 0; r0 < P; r0 += BM) {
         cx<T> acc[TM][TN];
 #pragma unroll
         for (int i = 0; i < TM; ++i)
 #pragma unroll
             for (int j = 0; j < TN; ++j) acc[i][j] = cx<T>{T(0), T(0)};
-        for (int k0 = 0; k0 < P; k0 += BK) {
-            for (int e = threadIdx.x; e < BM * BK; e += blockDim.x) {
-                int r = e / BK, kk = e % BK;
-                int gr = r0 + r, gk = k0 + kk;
-                As[e] = (gr < P && gk < P) ? A[(int64_t)gr * P + gk] : cx<T>{T(0), T(0)};
-            }
-            __syncthreads();
+        cx<T> nxt[G::LPT];
+        fetch(r0, 0, nxt);
+        put(0, nxt);
+        __syncthreads();
+        for (int kt = 0; kt < nk; ++kt) {
+            const int k0 = kt * BK, buf = kt & 1;
+            if (kt + 1 < nk) fetch(r0, k0 + BK, nxt);
+            const cx<T> *At = As + buf * BK * BMP;
             const int kmax = min(BK, P - k0);
             for (int kk = 0; kk < kmax; ++kk) {
                 cx<T> a[TM], x[TN];
-#pragma unroll
-                for (int i = 0; i < TM; ++i) a[i] = As[(ty * TM + i) * BK + kk];
-#pragma unroll
-                for (int j = 0; j < TN; ++j) x[j] = X[(k0 + kk) * BN + tx * TN + j];
+                lds_vec<T, TM>(At + kk * BMP + ty * TM, a);
+                lds_vec<T, TN>(X + (k0 + kk) * BN + tx * TN, x);
 #pragma unroll
                 for (int i = 0; i < TM; ++i)
 #pragma unroll
                     for (int j = 0; j < TN; ++j) cmac(acc[i][j], a[i], x[j]);
             }
+            if (kt + 1 < nk) put(buf ^ 1, nxt);
             __syncthreads();
         }
 #pragma unroll
@@ -77,8 +116,12 @@ __device__ __forceinline__ void tiled_gemm(int P, const cx<T> *__restrict__ A, c
 template <typename T>
 __device__ __forceinline__ void atomic_add_cx(cx<T> *o, cx<T> v)
 {
-    atomicAdd(&o->x, v.x);
-    atomicAdd(&o->y, v.y);
+    if constexpr (sizeof(T) == 4) {
+        atomicAdd((float2 *)o, make_float2(v.x, v.y));
+    } else {
+        atomicAdd(&o->x, v.x);
+        atomicAdd(&o->y, v.y);
+    }
 }
 
 // ------------------------------------------------------------- M2M / L2L
@@ -132,7 +175,7 @@ __global__ void __launch_bounds__(256) k_m2l(int p, const M2LWork *work, const G
     const int MW = 2 * p + 5;           // e^{i m phi}, m = -(p+2) .. p+2
     cx<T> *X = (cx<T> *)smraw;
     cx<T> *As = X + (size_t)P * BN;
-    cx<T> *E = As + 16 * TileCfg<T>::TM * TileCfg<T>::BK;   // [BN][MW]
+    cx<T> *E = As + 2 * GemmTile<T>::BK * GemmTile<T>::BMP;   // [BN][MW]
     short *NN = (short *)(E + BN * MW);                     // degree of index k
     M2LWork w = work[blockIdx.x];
     const GeomDev &g = geoms[w.geom];
@@ -222,8 +265,8 @@ template <typename T>
 static size_t gemm_smem(int p)
 {
     const int P = (p + 1) * (p + 1);
-    constexpr int BN = 16 * TileCfg<T>::TN, BM = 16 * TileCfg<T>::TM, BK = TileCfg<T>::BK;
-    return ((size_t)P * BN + (size_t)BM * BK + (size_t)BN * (2 * p + 5)) * sizeof(cx<T>) +
+    using G = GemmTile<T>;
+    return ((size_t)P * G::BN + (size_t)2 * G::BK * G::BMP + (size_t)G::BN * (2 * p + 5)) * sizeof(cx<T>) +
            (size_t)P * sizeof(short) + 16;
 }
 
