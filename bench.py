@@ -57,6 +57,8 @@ def workload(name, seed_shift=0):
         return W.four_layer_clusters(seed=1005 + seed_shift), dict(depth=6, theta=0.55)
     if name == "three_layer":
         return W.three_layer(seed=1002 + seed_shift), dict(depth=5, theta=0.55)
+    if name == "four_layer_small":
+        return W.four_layer_clusters(n=131072, seed=1005 + seed_shift), dict(depth=4, theta=0.55)
     if name == "three_layer_small":
         return W.three_layer(n=8192, seed=1002 + seed_shift, p=8), dict(depth=4, theta=0.55)
     if name == "two_layer":

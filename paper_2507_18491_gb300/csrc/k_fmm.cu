@@ -115,6 +115,22 @@ template <typename T>
 __device__ inline void point_seed(int p, cd k, double dx, double dy, double dz, bool conjugate,
                                   double scale, double inv_s, cx<T> *jr, T *geo, cx<T> *kz)
 {
+    if constexpr (sizeof(T) == 4) {
+        // mixed form: angles and k r in FP32 (the FP64 pipe is 1/64 of the FP32 one)
+        const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
+        const float rxy = sqrtf(fx * fx + fy * fy), r = sqrtf(fx * fx + fy * fy + fz * fz);
+        const cf kf{(float)k.x, (float)k.y};
+        const cf kr = r * kf;
+        if (abs2(kr) < 2.25f) {
+            geo[0] = r > 0.f ? fz / r : 1.f;
+            geo[1] = r > 0.f ? rxy / r : 0.f;
+            geo[2] = rxy > 0.f ? fx / rxy : 1.f;
+            geo[3] = rxy > 0.f ? (conjugate ? -fy : fy) / rxy : 0.f;
+            kz[0] = cx<T>{kr.x, kr.y};
+            kz[1] = (r * (float)inv_s) * cx<T>{kf.x, kf.y};
+            return;
+        }
+    }
     const double r = sqrt(dx * dx + dy * dy + dz * dz);
     const double rxy = sqrt(dx * dx + dy * dy);
     geo[0] = (T)(r > 0 ? dz / r : 1.0);
@@ -122,11 +138,7 @@ __device__ inline void point_seed(int p, cd k, double dx, double dy, double dz, 
     geo[2] = (T)(rxy > 0 ? dx / rxy : 1.0);
     geo[3] = (T)(rxy > 0 ? (conjugate ? -dy : dy) / rxy : 0.0);
     const cd kr = k * r;
-    if (sizeof(T) == 4 && cabsd(kr) < 1.5) {
-        const cd zeta = (r * inv_s) * k;
-        kz[0] = cx<T>{(T)kr.x, (T)kr.y};
-        kz[1] = cx<T>{(T)zeta.x, (T)zeta.y};
-    } else {
+    {
         kz[0] = cx<T>{T(-1), T(0)};   // marker: jr already set
         cd jd[LMF_PMAX + 1];
         sph_bessel_seq(kr, p, jd);
@@ -656,6 +668,11 @@ cudaError_t configure_fmm_kernels()
     if ((e = cudaFuncSetAttribute(k_p2m<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_l2p<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_l2p<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    const int mx = (int)cudaSharedmemCarveoutMaxShared;
+    if ((e = cudaFuncSetAttribute(k_p2m<float>, cudaFuncAttributePreferredSharedMemoryCarveout, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_p2m<double>, cudaFuncAttributePreferredSharedMemoryCarveout, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_l2p<float>, cudaFuncAttributePreferredSharedMemoryCarveout, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_l2p<double>, cudaFuncAttributePreferredSharedMemoryCarveout, mx))) return e;
     return configure_trans_kernels();
 }
 }  // namespace lmf

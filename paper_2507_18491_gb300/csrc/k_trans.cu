@@ -24,17 +24,19 @@ template <typename T> struct TileCfg;
 template <> struct TileCfg<float> { static constexpr int TM = 4, TN = 4, BK = 16; };
 template <> struct TileCfg<double> { static constexpr int TM = 4, TN = 2, BK = 16; };
 
-// Y(P x BN) = A(P x P, row-major, global) X(P x BN, shared); 256 threads as a
+// Y(P x BN) = A(P x P, row-major, global) X(P x BN, shared, rows BNP apart); 256 threads as a
 // 16 x 16 grid, each owning TM rows x TN columns.  A streams through two
 // shared-memory tiles of BK x BM (k-major, rows padded to BMP so that the
 // transposing stores spread over banks and every thread's TM rows stay 16-byte
 // aligned); the next tile is fetched into registers while the current one is
 // multiplied.  The TM rows and TN columns of a thread are read with 16-byte
-// loads.  store(r, c, y) for r < P, c < ncol.
+// loads.  One CTA computes the BM rows of row tile r_tile; store(r, c, y) for
+// r < P, c < ncol.
 template <typename T>
 struct GemmTile {
     static constexpr int TM = TileCfg<T>::TM, TN = TileCfg<T>::TN, BK = TileCfg<T>::BK;
     static constexpr int BM = 16 * TM, BN = 16 * TN, BMP = BM + 2;
+    static constexpr int BNP = BN + 2;          // row stride of X in shared memory
     static constexpr int LPT = BM * BK / 256;   // tile elements loaded per thread
 };
 
@@ -51,7 +53,7 @@ __device__ __forceinline__ void lds_vec(const cx<T> *src, cx<T> (&dst)[N])
 }
 
 template <typename T, typename Store>
-__device__ __forceinline__ void tiled_gemm(int P, const cx<T> *__restrict__ A, const cx<T> *X,
+__device__ __forceinline__ void tiled_gemm(int P, int r_tile, const cx<T> *__restrict__ A, const cx<T> *X,
                                            cx<T> *As, int ncol, Store store)
 {
     using G = GemmTile<T>;
@@ -73,7 +75,8 @@ __device__ __forceinline__ void tiled_gemm(int P, const cx<T> *__restrict__ A, c
             As[buf * BK * BMP + kk * BMP + r] = v[u];
         }
     };
-    for (int r0 = 0; r0 < P; r0 += BM) {
+    {
+        const int r0 = r_tile * BM;
         cx<T> acc[TM][TN];
 #pragma unroll
         for (int i = 0; i < TM; ++i)
@@ -91,7 +94,7 @@ __device__ __forceinline__ void tiled_gemm(int P, const cx<T> *__restrict__ A, c
             for (int kk = 0; kk < kmax; ++kk) {
                 cx<T> a[TM], x[TN];
                 lds_vec<T, TM>(At + kk * BMP + ty * TM, a);
-                lds_vec<T, TN>(X + (k0 + kk) * BN + tx * TN, x);
+                lds_vec<T, TN>(X + (k0 + kk) * G::BNP + tx * TN, x);
 #pragma unroll
                 for (int i = 0; i < TM; ++i)
 #pragma unroll
@@ -132,22 +135,35 @@ __global__ void __launch_bounds__(256) k_group_gemm(int p, const GemmWork *work,
                                                     const int64_t *src, const int64_t *dst,
                                                     const cx<T> *in, cx<T> *out, int atomic)
 {
-    constexpr int BN = 16 * TileCfg<T>::TN;
+    using G = GemmTile<T>;
+    constexpr int BN = G::BN, BNP = G::BNP;
     extern __shared__ unsigned char smraw[];
     const int P = (p + 1) * (p + 1);
     cx<T> *X = (cx<T> *)smraw;
-    cx<T> *As = X + (size_t)P * BN;
+    cx<T> *As = X + (size_t)P * BNP;
     GemmWork w = work[blockIdx.x];
     const int ncol = 3 * w.npair;
-    for (int e = threadIdx.x; e < P * BN; e += blockDim.x) {
-        int k = e / BN, col = e % BN;
-        cx<T> v{T(0), T(0)};
-        if (col < ncol) v = in[(src[w.pair0 + col / 3] * 3 + col % 3) * P + k];
-        X[e] = v;
+    // gather the columns: consecutive threads read consecutive coefficients of
+    // one expansion; loads are issued in batches of GB before their stores
+    constexpr int GB = 8;
+    const int ne = P * BN;
+    for (int e0 = threadIdx.x; e0 < ne; e0 += GB * blockDim.x) {
+        cx<T> v[GB];
+#pragma unroll
+        for (int u = 0; u < GB; ++u) {
+            const int e = e0 + u * blockDim.x, col = e / P, k = e - col * P;
+            v[u] = cx<T>{T(0), T(0)};
+            if (e < ne && col < ncol) v[u] = in[(src[w.pair0 + col / 3] * 3 + col % 3) * P + k];
+        }
+#pragma unroll
+        for (int u = 0; u < GB; ++u) {
+            const int e = e0 + u * blockDim.x, col = e / P, k = e - col * P;
+            if (e < ne) X[k * BNP + col] = v[u];
+        }
     }
     __syncthreads();
     const cx<T> *A = mats + (int64_t)w.group * P * P;
-    tiled_gemm<T>(P, A, X, As, ncol, [&](int r, int c, cx<T> y) {
+    tiled_gemm<T>(P, blockIdx.y, A, X, As, ncol, [&](int r, int c, cx<T> y) {
         cx<T> *o = out + (dst[w.pair0 + c / 3] * 3 + c % 3) * P + r;
         if (atomic) atomic_add_cx(o, y);
         else *o += y;
@@ -174,7 +190,7 @@ __global__ void __launch_bounds__(256) k_m2l(int p, const M2LWork *work, const G
     const int P = (p + 1) * (p + 1);
     const int MW = 2 * p + 5;           // e^{i m phi}, m = -(p+2) .. p+2
     cx<T> *X = (cx<T> *)smraw;
-    cx<T> *As = X + (size_t)P * BN;
+    cx<T> *As = X + (size_t)P * GemmTile<T>::BNP;
     cx<T> *E = As + 2 * GemmTile<T>::BK * GemmTile<T>::BMP;   // [BN][MW]
     short *NN = (short *)(E + BN * MW);                     // degree of index k
     M2LWork w = work[blockIdx.x];
@@ -217,11 +233,11 @@ __global__ void __launch_bounds__(256) k_m2l(int p, const M2LWork *work, const G
             if ((sneg && (e1 & 1)) != (c.has_src_refl && (e1 & 1))) sc = -sc;
             v = sc * (E[pp * MW + (p + 2) + ms] * x);
         }
-        X[e] = v;
+        X[k * GemmTile<T>::BNP + col] = v;
     }
     __syncthreads();
     const cx<T> *A = tab + ((int64_t)g.tab_index * NTAB + t) * P * P;
-    tiled_gemm<T>(P, A, X, As, ncol, [&](int r, int col, cx<T> y) {
+    tiled_gemm<T>(P, blockIdx.y, A, X, As, ncol, [&](int r, int col, cx<T> y) {
         int pp = col / ncpp, j = col % ncpp;
         ColSpec cs = c_cols[t][j];
         int nu = NN[r], mh = r - nu * nu - nu;
@@ -266,7 +282,7 @@ static size_t gemm_smem(int p)
 {
     const int P = (p + 1) * (p + 1);
     using G = GemmTile<T>;
-    return ((size_t)P * G::BN + (size_t)2 * G::BK * G::BMP + (size_t)G::BN * (2 * p + 5)) * sizeof(cx<T>) +
+    return ((size_t)P * G::BNP + (size_t)2 * G::BK * G::BMP + (size_t)G::BN * (2 * p + 5)) * sizeof(cx<T>) +
            (size_t)P * sizeof(short) + 16;
 }
 
@@ -284,7 +300,8 @@ void launch_group_gemm_t(int p, int64_t nwork, const GemmWork *work, const cx<T>
                          bool atomic, cudaStream_t st)
 {
     if (nwork <= 0) return;
-    k_group_gemm<T><<<(unsigned)nwork, 256, gemm_smem<T>(p), st>>>(p, work, mats, src, dst, in,
+    const unsigned nrt = (unsigned)(((p + 1) * (p + 1) + GemmTile<T>::BM - 1) / GemmTile<T>::BM);
+    k_group_gemm<T><<<dim3((unsigned)nwork, nrt), 256, gemm_smem<T>(p), st>>>(p, work, mats, src, dst, in,
                                                                     out, atomic);
 }
 
@@ -294,7 +311,8 @@ void launch_m2l_t(int p, int64_t nwork, const M2LWork *work, const GeomDev *geom
                   cx<T> *le, cudaStream_t st)
 {
     if (nwork <= 0) return;
-    k_m2l<T><<<(unsigned)nwork, 256, gemm_smem<T>(p), st>>>(p, work, geoms, comps, pairs, tab, me,
+    const unsigned nrt = (unsigned)(((p + 1) * (p + 1) + GemmTile<T>::BM - 1) / GemmTile<T>::BM);
+    k_m2l<T><<<dim3((unsigned)nwork, nrt), 256, gemm_smem<T>(p), st>>>(p, work, geoms, comps, pairs, tab, me,
                                                              le);
 }
 
@@ -332,6 +350,12 @@ cudaError_t configure_trans_kernels()
     if ((e = cudaFuncSetAttribute(k_group_gemm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_m2l<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_m2l<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    // these CTAs hold ~100 KB of shared memory: take the whole carveout so that two fit on an SM
+    const int mx = (int)cudaSharedmemCarveoutMaxShared;
+    if ((e = cudaFuncSetAttribute(k_group_gemm<float>, cudaFuncAttributePreferredSharedMemoryCarveout, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_group_gemm<double>, cudaFuncAttributePreferredSharedMemoryCarveout, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_m2l<float>, cudaFuncAttributePreferredSharedMemoryCarveout, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_m2l<double>, cudaFuncAttributePreferredSharedMemoryCarveout, mx))) return e;
     return configure_m2l_tc();
 }
 
