@@ -44,7 +44,7 @@ struct DevState {
     std::vector<int64_t> twork_off;
     NearPair *near = nullptr;
     cd *s2t = nullptr;               // near field: 8 combined coefficients per point pair
-    S2TWork *s2twork = nullptr;      // near-field work items
+    S2TRow *s2twork = nullptr;       // near-field target rows
     int64_t n_s2twork = 0;
     int *flag = nullptr;
     int *mvstatus = nullptr;         // matvec status word (bit 4: tensor-core wait gave up)
@@ -642,13 +642,12 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(st));
         dfree(ctx, s2t5);
-        std::vector<S2TWork> sw;
+        std::vector<S2TRow> sw;
         for (size_t i = 0; i < ctx->near.size(); ++i) {
             const NearPair &q = ctx->near[i];
             const Box &bs = ctx->boxes[q.src], &bt = ctx->boxes[q.tgt];
-            for (int64_t t0 = 0; t0 < bt.p1 - bt.p0; t0 += S2T_BLK)
-                for (int64_t s0 = 0; s0 < bs.p1 - bs.p0; s0 += S2T_BLK)
-                    sw.push_back(S2TWork{(int64_t)i, (int)t0, (int)s0});
+            for (int64_t s0 = 0; s0 < bs.p1 - bs.p0; s0 += S2T_SRC)
+                for (int64_t ii = 0; ii < bt.p1 - bt.p0; ++ii) sw.push_back(S2TRow{(int64_t)i, (int)ii, (int)s0});
         }
         TRY(dupload(ctx, &d->s2twork, sw));
         d->n_s2twork = (int64_t)sw.size();
@@ -732,7 +731,8 @@ static lmfmm_status matvec_t(lmfmm_ctx *ctx, const lmfmm_c128 *J, lmfmm_c128 *Ph
             }
         }
         int64_t w0 = d->gwork_off[lev], w1 = d->gwork_off[lev + 1];
-        launch_group_gemm_t<T>(p, w1 - w0, d->gwork + w0, tdn, d->tparent, d->tchild, le, le, false,
+        // a child has one parent: reductions (fire and forget) rather than read-modify-write
+        launch_group_gemm_t<T>(p, w1 - w0, d->gwork + w0, tdn, d->tparent, d->tchild, le, le, true,
                                st);
     }
     CK(cudaEventRecord(d->ev[4], st));

@@ -599,25 +599,26 @@ __global__ void k_s2t_combine(const NearPair *near, const BoxDev *boxes, const d
     }
 }
 
-// Phi_h(i) += near-field terms of k_s2t_combine's coefficients.  One CTA per
-// work item: up to S2T_BLK targets (one per thread) of one near pair against
-// up to S2T_BLK of its sources, so that crowded box pairs spread over many
-// CTAs; charges are broadcast across the warp, coefficients coalesced over
-// targets.
-__global__ void k_s2t_apply8(const S2TWork *work, const NearPair *near, const BoxDev *boxes,
-                             const cd *coef8, const cd *qh, cd *ph)
+// Phi_h(i) += near-field terms of k_s2t_combine's coefficients.  One thread per
+// target row (a target of one near pair against a block of up to S2T_SRC of
+// the pair's sources), rows of a pair on consecutive threads: the coefficients
+// are read coalesced over targets and the charges are broadcast; small box
+// pairs share CTAs, crowded ones spread over many.
+__global__ void __launch_bounds__(256) k_s2t_apply8(int64_t nrow, const S2TRow *rows, const NearPair *near,
+                                                    const BoxDev *boxes, const cd *coef8, const cd *qh, cd *ph)
 {
-    const S2TWork w = work[blockIdx.x];
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= nrow) return;
+    const S2TRow w = rows[e];
     const NearPair np = near[w.pair];
     const BoxDev B = boxes[np.src], C = boxes[np.tgt];
-    const int64_t nC = C.p1 - C.p0;
-    const int64_t ii = w.t0 + threadIdx.x;
-    const int64_t j1 = min((int64_t)w.s0 + S2T_BLK, B.p1 - B.p0);
-    if (ii >= nC) return;
-    const cd *K = coef8 + np.coef0 * 8;
+    const int64_t nC = C.p1 - C.p0, j1 = min((int64_t)w.s0 + S2T_SRC, B.p1 - B.p0);
+    const int64_t ii = w.ii;
+    const cd *K = coef8 + np.coef0 * 8 + ii;
     cd A = mkd(0.0), Bv = mkd(0.0), Cv = mkd(0.0);
+#pragma unroll 4
     for (int64_t jj = w.s0; jj < j1; ++jj) {
-        const cd *k = K + jj * 8 * nC + ii;
+        const cd *k = K + jj * 8 * nC;
         const int64_t sj = B.p0 + jj;
         const cd a = qh[3 * sj], b = qh[3 * sj + 1], c = qh[3 * sj + 2];
         const cd k0 = k[0], k1 = k[nC], k2 = k[2 * nC], k3 = k[3 * nC], k4 = k[4 * nC], k5 = k[5 * nC],
@@ -642,11 +643,11 @@ void launch_s2t_combine(int64_t nnear, const NearPair *near, const BoxDev *boxes
     k_s2t_combine<<<(unsigned)nnear, 128, 0, st>>>(near, boxes, xyz, coef5, coef8);
 }
 
-void launch_s2t_apply8(int64_t nwork, const S2TWork *work, const NearPair *near, const BoxDev *boxes,
+void launch_s2t_apply8(int64_t nrow, const S2TRow *rows, const NearPair *near, const BoxDev *boxes,
                        const cd *coef8, const cd *qh, cd *phih, cudaStream_t st)
 {
-    if (nwork <= 0) return;
-    k_s2t_apply8<<<(unsigned)nwork, S2T_BLK, 0, st>>>(work, near, boxes, coef8, qh, phih);
+    if (nrow <= 0) return;
+    k_s2t_apply8<<<(unsigned)((nrow + 255) / 256), 256, 0, st>>>(nrow, rows, near, boxes, coef8, qh, phih);
 }
 
 void launch_s2t_apply(int64_t nnear, const NearPair *near, const BoxDev *boxes,

@@ -131,14 +131,15 @@ void launch_s2t_pre(int64_t nnear, const NearPair *near, const BoxDev *boxes, co
 // matvec near field: 8 combined coefficients per point pair ([j][8][i] per near pair)
 void launch_s2t_combine(int64_t nnear, const NearPair *near, const BoxDev *boxes, const double *xyz,
                         const cd *coef5, cd *coef8, cudaStream_t st);
-// work item of the matvec near field: targets [t0, t0 + S2T_BLK) of near pair
-// `pair` against its sources [s0, s0 + S2T_BLK)
-constexpr int S2T_BLK = 64;
-struct S2TWork {
+// one target row of the matvec near field: target ii of near pair `pair`
+// against the pair's sources [s0, s0 + S2T_SRC); rows are ordered by pair,
+// then source block, then ii
+constexpr int S2T_SRC = 64;
+struct S2TRow {
     int64_t pair;
-    int t0, s0;
+    int ii, s0;
 };
-void launch_s2t_apply8(int64_t nwork, const S2TWork *work, const NearPair *near, const BoxDev *boxes,
+void launch_s2t_apply8(int64_t nrow, const S2TRow *rows, const NearPair *near, const BoxDev *boxes,
                        const cd *coef8, const cd *qh, cd *phih, cudaStream_t st);
 void launch_s2t_apply(int64_t nnear, const NearPair *near, const BoxDev *boxes,
                       const double *xyz, const cd *coef, const cd *qh, cd *phih,
