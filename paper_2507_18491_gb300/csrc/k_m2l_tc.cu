@@ -411,6 +411,7 @@ constexpr int V2_PT = 128 * V2_PG; // producer threads
 constexpr int V2_ET = 256;         // epilogue threads
 constexpr int V2_EW = V2_ET / 32;  // epilogue warps
 constexpr int V2_RJ = (V2_NR_MAX + 31) / 32;   // rows per lane of a column in the scatter
+constexpr int V2_DS = 34;          // row stride (words) of an epilogue warp's 16-row drain tile
 constexpr int V2_WTMA = (V2_PT + V2_ET) / 32, V2_WMMA = V2_WTMA + 1;
 constexpr int V2_THREADS = (V2_WMMA + 1) * 32;
 constexpr uint32_t V2_SMEM_MAX = 227 * 1024;
@@ -421,7 +422,7 @@ struct V2Col {
 };
 
 struct V2Plan {
-    uint32_t NR, nchunk, SB, CB, ST, MO, g_bytes, cols_bytes, meta_bytes, meta, tabs, mm_n, bars, total;
+    uint32_t NR, nchunk, SB, CB, ST, MO, g_bytes, cols_bytes, meta_bytes, meta, tabs, mm_n, dtile, bars, total;
 };
 
 __host__ __device__ inline V2Plan v2_plan(int p)
@@ -437,12 +438,15 @@ __host__ __device__ inline V2Plan v2_plan(int p)
     s.cols_bytes = BN * (uint32_t)sizeof(V2Col);
     s.meta_bytes = 2 * s.g_bytes + s.cols_bytes;    // G, O, column records
     s.mm_n = V2_KC * s.nchunk;                      // order table, whole chunks (>= P)
-    const uint32_t fixed = 2 * s.meta_bytes + 2 * s.mm_n + 32 + (2 * V2_ST_MAX + 2 * V2_SX + 12) * 8 + 16;
+    const uint32_t dtile_bytes = V2_EW * 16 * V2_DS * 4;   // per epilogue warp: 16 rows x 32 lanes
+    const uint32_t fixed =
+        2 * s.meta_bytes + 2 * s.mm_n + 32 + dtile_bytes + 16 + (2 * V2_ST_MAX + 2 * V2_SX + 12) * 8 + 16;
     uint32_t st = (V2_SMEM_MAX - fixed) / s.CB;
     s.ST = st > V2_ST_MAX ? V2_ST_MAX : st;
     s.meta = s.ST * s.CB;
     s.tabs = (s.meta + 2 * s.meta_bytes + 15) & ~15u;
-    s.bars = (s.tabs + 2 * s.mm_n + 15) & ~15u;
+    s.dtile = (s.tabs + 2 * s.mm_n + 15) & ~15u;
+    s.bars = (s.dtile + dtile_bytes + 15) & ~15u;
     s.total = s.bars + (2 * V2_ST_MAX + 2 * V2_SX + 12) * 8 + 16;
     return s;
 }
@@ -866,7 +870,6 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
         // ------------------------------------------------ epilogue
         const int ea = tid - V2_PT;                   // 0 .. V2_ET-1
         const int q4 = warp & 3, half = ea / 128;     // lane quadrant, slab parity
-        const int e = 32 * q4 + lane;                 // real column = tensor-memory lane
         const uint32_t lane_base = tbase + ((uint32_t)(32 * q4) << 16);
         const int ew = ea >> 5;                       // epilogue warp 0 .. V2_EW-1
         int rm[V2_RJ];                                // order m of rows lane + 32 i
@@ -896,27 +899,29 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
                 break;
             }
             tc::fence_after();
-            // scratch layout [column cc][row r] complex: the two lanes of a column
-            // swap values so that each store of the pair fills one 32-byte sector
-            // (lane b writes rows 4j + 2b, 4j + 2b + 1 of the slab)
-            const int b = lane & 1;
-            float2 *Yc = (float2 *)Y + (size_t)(e >> 1) * NR;
+            // scratch layout [column cc][row r] complex.  A 16-row slab of the warp's
+            // 32 real columns goes through the warp's shared-memory tile so that each
+            // 16-byte store instruction writes four whole 128-byte column segments
+            // (lane L: column 4h + L/8 of the warp's 16, rows 2 (L % 8), + 1)
+            float *T = (float *)(smraw + sp.dtile) + (ea >> 5) * 16 * V2_DS;
+            float4 *Yq = (float4 *)((float2 *)Y + (size_t)(16 * q4) * NR);
+            const int lr = 2 * (lane & 7), lc = lane >> 3;
             for (int c0 = 16 * half; c0 < NR; c0 += 32) {   // NR is a multiple of 16
                 uint32_t va[16], vb[16];
                 tc::tmem_ld16(lane_base + c0, va);
                 tc::tmem_ld16(lane_base + NR + c0, vb);
                 tc::tmem_ld_wait();
-                float v[16];
 #pragma unroll
-                for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(va[i]) + __uint_as_float(vb[i]);
+                for (int i = 0; i < 16; ++i) T[i * V2_DS + lane] = __uint_as_float(va[i]) + __uint_as_float(vb[i]);
+                __syncwarp();
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const float r0 = __shfl_xor_sync(0xffffffffu, b ? v[4 * j] : v[4 * j + 2], 1);
-                    const float r1 = __shfl_xor_sync(0xffffffffu, b ? v[4 * j + 1] : v[4 * j + 3], 1);
-                    const float4 o = b ? make_float4(r0, v[4 * j + 2], r1, v[4 * j + 3])
-                                       : make_float4(v[4 * j], r0, v[4 * j + 1], r1);
-                    *(float4 *)(Yc + c0 + 4 * j + 2 * b) = o;
+                for (int h = 0; h < 4; ++h) {
+                    const int cl = 4 * h + lc;
+                    const float2 x0 = *(const float2 *)(T + lr * V2_DS + 2 * cl);
+                    const float2 x1 = *(const float2 *)(T + (lr + 1) * V2_DS + 2 * cl);
+                    Yq[((size_t)cl * NR + c0 + lr) >> 1] = make_float4(x0.x, x0.y, x1.x, x1.y);
                 }
+                __syncwarp();
             }
             tc::fence_before();
             tc::mbar_arrive(accempty);
