@@ -277,10 +277,10 @@ def main():
     launches_per_step = 6 + 2 * st["depth"]
     kern = {0: "k_m2l<double>", 1: "k_m2l<float>", 2: "k_m2l_tc", 3: "k_m2l_tc2"}[st["m2l_kernel"]]
     # DRAM bytes per launch of k_m2l_tc2: the table image times the read+write / image
-    # ratio of an ncu capture of the same kernel (dram__bytes_read.sum 6.412 GB +
-    # dram__bytes_write.sum 0.128 GB for a 6.247 GB image, four-layer N = 131072,
+    # ratio of an ncu capture of the same kernel (dram__bytes_read.sum 3.864 GB +
+    # dram__bytes_write.sum 0.067 GB for a 3.691 GB image, three-layer N = 8192,
     # p = 12, depth 4); other kernels: not captured
-    traffic = st["bytes_tables"] * (6.540 / 6.247) if st["m2l_kernel"] == 3 else None
+    traffic = st["bytes_tables"] * (3.931 / 3.691) if st["m2l_kernel"] == 3 else None
     bound = "tensor" if st["m2l_kernel"] >= 2 else "alu"
     if prec == lmfmm.FP64:
         peak, peak_src = FP64_PEAK_TFLOPS, "derived FP64 ALU: 152 SM x 2 FMA/clk x 2 x 2070 MHz"
