@@ -57,7 +57,7 @@ __device__ __forceinline__ void tiled_gemm(int P, int r_tile, const cx<T> *__res
                                            cx<T> *As, int ncol, Store store)
 {
     using G = GemmTile<T>;
-    constexpr int TM = G::TM, TN = G::TN, BK = G::BK, BM = G::BM, BN = G::BN, BMP = G::BMP;
+    constexpr int TM = G::TM, TN = G::TN, BK = G::BK, BM = G::BM, BMP = G::BMP;
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     const int nk = (P + BK - 1) / BK;
     auto fetch = [&](int r0, int k0, cx<T> (&v)[G::LPT]) {
@@ -277,6 +277,16 @@ __global__ void k_scale_tables(int p, int64_t g0, int64_t ng, const GeomDev *geo
 }
 
 // ---------------------------------------------------------------- launchers
+// shared memory of k_group_gemm: the gathered columns and two tiles of the matrix
+template <typename T>
+static size_t group_gemm_smem(int p)
+{
+    using G = GemmTile<T>;
+    const size_t P = (size_t)(p + 1) * (p + 1);
+    return (P * G::BNP + (size_t)2 * G::BK * G::BMP) * sizeof(cx<T>);
+}
+
+// shared memory of k_m2l: as k_group_gemm, plus the pair phases and the degree table
 template <typename T>
 static size_t gemm_smem(int p)
 {
@@ -301,7 +311,7 @@ void launch_group_gemm_t(int p, int64_t nwork, const GemmWork *work, const cx<T>
 {
     if (nwork <= 0) return;
     const unsigned nrt = (unsigned)(((p + 1) * (p + 1) + GemmTile<T>::BM - 1) / GemmTile<T>::BM);
-    k_group_gemm<T><<<dim3((unsigned)nwork, nrt), 256, gemm_smem<T>(p), st>>>(p, work, mats, src, dst, in,
+    k_group_gemm<T><<<dim3((unsigned)nwork, nrt), 256, group_gemm_smem<T>(p), st>>>(p, work, mats, src, dst, in,
                                                                     out, atomic);
 }
 
