@@ -271,7 +271,7 @@ constexpr size_t LEAF_SMEM_CAP = 200 * 1024;   // dynamic shared memory granted 
 // whole CTA, then each thread accumulates its multipole coefficients over the
 // chunk's points.
 template <typename T>
-__global__ void __launch_bounds__(256) k_p2m(int p, int CH, const int64_t *leaves, const BoxDev *boxes,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_p2m(int p, int CH, const int64_t *leaves, const BoxDev *boxes,
                                              const double *xyz, const cd *qh, MediumDev M, LayerScale ls,
                                              cx<T> *me)
 {
