@@ -599,6 +599,10 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
     const int P = (p + 1) * (p + 1);
     const V2Plan sp = v2_plan(p);
     const int NR = (int)sp.NR, nchunk = (int)sp.nchunk, ST = (int)sp.ST, MO = (int)sp.MO;
+    // translations take the inputs from the highest degrees down: the accumulator
+    // truncates relative to its running sum, so the dominant low-degree terms come
+    // last and the low-degree outputs see few truncations at full size
+    const bool krev = mode == 1;
     short *MM = (short *)(smraw + sp.tabs);   // order m of index k = n^2 + n + m (0 beyond P)
     uint64_t *bars = (uint64_t *)(smraw + sp.bars);
     uint64_t *tfull = bars, *tempty = bars + V2_ST_MAX, *xfull = bars + 2 * V2_ST_MAX,
@@ -663,7 +667,8 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
                         break;
                     }
                     tc::mbar_expect_tx(&tfull[s], sp.CB);
-                    tc::bulk_g2s(smraw + s * sp.CB, src + (size_t)c * sp.CB, sp.CB, &tfull[s]);
+                    tc::bulk_g2s(smraw + s * sp.CB, src + (size_t)(krev ? nchunk - 1 - c : c) * sp.CB, sp.CB,
+                                 &tfull[s]);
                     ++g;
                     if (++s == ST) {
                         s = 0;
@@ -785,6 +790,7 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
                 }
             };
             auto fetch = [&](int ch, float2(&v)[KH]) {
+                if (krev) ch = nchunk - 1 - ch;
                 int mo[KC];
                 orders(ch, mo);
 #pragma unroll
@@ -803,7 +809,7 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
                 for (int u = 0; u < V2_D; ++u) {
                     const int qq = q0 + u;
                     if (qq >= nmine) break;
-                    const int ch = cfirst + qq * V2_PG;
+                    const int ch = krev ? nchunk - 1 - (cfirst + qq * V2_PG) : cfirst + qq * V2_PG;   // data chunk
                     bool okw = !xwrapped || tc::mbar_wait(&xempty[xs], xph ^ 1, WAIT_POLLS);
                     if (__any_sync(0xffffffffu, !okw)) {
                         failed = true;
