@@ -213,8 +213,9 @@ def main():
     ap.add_argument("--workload", default="four_layer")
     ap.add_argument("--p", type=int, default=0)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--tensor-cores", type=int, default=None,
-                    help="tensor_cores option of the mixed form (default: the operator's)")
+    ap.add_argument("--tensor-cores", type=int, default=3,
+                    help="tensor_cores option of the mixed form: 3 = M2L, M2M and L2L on the "
+                         "tensor cores (default), 1 = M2L only, 0 = none")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -229,7 +230,7 @@ def main():
     p = args.p or w.p
     prec = lmfmm.FP64 if args.precision == "fp64" else lmfmm.MIXED
     t0 = time.time()
-    tck = {} if args.tensor_cores is None else {"tensor_cores": args.tensor_cores}
+    tck = {"tensor_cores": args.tensor_cores} if prec == lmfmm.MIXED else {}
     op = lmfmm.Operator(w.d, w.k, w.xyz, p=p, depth=opt["depth"], theta=opt["theta"],
                         precision=prec, device=dev, **tck).build()
     setup_s = time.time() - t0
@@ -294,7 +295,8 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if prec == lmfmm.FP64 else "f32", "data": "synthetic",
         "config": {"workload": w.name, "N": w.N, "layers": int(w.d.size + 1), "p": p,
-                   "depth": st["depth"], "theta": opt["theta"], "precision": args.precision, "tensor_cores": int(args.tensor_cores if args.tensor_cores is not None else 1),
+                   "depth": st["depth"], "theta": opt["theta"], "precision": args.precision,
+                   "tensor_cores": int(args.tensor_cores) if prec == lmfmm.MIXED else 0,
                    "components": st["n_components"], "m2l_pairs": st["n_m2l_pairs"],
                    "geometries": st["n_geometries"], "near_point_pairs": st["n_near_point_pairs"],
                    "setup_s": round(setup_s, 3), "l2": "flushed (256 MiB write) between steps",
