@@ -245,9 +245,10 @@ def test_tensor_core_m2l(p):
 
 
 def test_tensor_core_translations():
-    """tensor_cores = 3 also runs M2M / L2L on the persistent tensor-core kernel:
-    within a looser bar of the FP64 form (the truncating tensor-core accumulation
-    compounds along the tree), and close to the default mixed form."""
+    """tensor_cores = 3 also runs M2M / L2L on the persistent tensor-core kernel.
+    Its truncating accumulation compounds along the tree; taking the inputs from
+    the highest degree down keeps the added error small: within 1.5x the error of
+    the M2L-only tensor-core form against the FP64 form, and close to that form."""
     w = W.three_layer(n=8192, p=12, depth=4)
     Jt = torch.from_numpy(w.J).cuda()
     kw = dict(p=12, depth=4, theta=0.5)
@@ -261,7 +262,7 @@ def test_tensor_core_translations():
         out[tc] = op.matvec(Jt).cpu().numpy()
         op.close()
     print("M2L only %.3e  with translations %.3e" % (rel(out[1], a), rel(out[3], a)))
-    assert rel(out[3], a) < 5e-6
+    assert rel(out[3], a) < 1.5 * rel(out[1], a) + 1e-7
     assert rel(out[3], out[1]) < 5e-6
 
 
