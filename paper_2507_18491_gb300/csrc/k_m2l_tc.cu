@@ -1,6 +1,9 @@
-// M2L of the mixed form on the 5th-generation tensor cores (tcgen05).
+// M2L (and, in translation mode, M2M / L2L) of the mixed form on the
+// 5th-generation tensor cores (tcgen05).  Two kernels: k_m2l_tc2 (v2 below,
+// persistent, three-piece bf16 operands, p <= 12) and k_m2l_tc (this part,
+// streamed operands, TF32 hi/lo, p <= 15).
 //
-// A work item applies one scaled table A (P x P complex, row (nu,mu), column
+// k_m2l_tc: a work item applies one scaled table A (P x P complex, row (nu,mu), column
 // (n',m')) to up to 64 phase-shifted source expansions, exactly as the FP32
 // SIMT kernel does, but the product runs as a real GEMM in which every
 // complex entry a becomes the 2 x 2 block [[Re a, -Im a], [Im a, Re a]]:
@@ -369,9 +372,10 @@ __global__ void __launch_bounds__(NT) k_m2l_tc(int p, int MT, uint32_t tmem_cols
 // (Im x, Re x) of complex column c, giving Re (T' x) and Im (T' x) -- and
 // whose NR >= P columns are the table rows (nu, mu).  The table enters as
 // the B operand unchanged in shape (K = interleaved Re/Im input index); it
-// is stored once per build as TF32 hi/lo planes in exactly the shared-memory
-// image of each K-chunk, with the factors of the M2L that depend only on the
-// degrees folded in:
+// is stored once per build as three bf16 planes (x ~ x1 + x2 + x3, each the
+// bf16 rounding of what the previous pieces leave) in exactly the
+// shared-memory image of each K-step, with the factors of the M2L that depend
+// only on the degrees folded in:
 //   T'[nu mu][n' m'] = (-i)^nu f_t^nu  T[nu mu][n' m']  i^n' f_s^n'
 // (f = -1 where a downward component or a mirrored box flips odd powers,
 // else 1; these are exact in any precision).  What is left per column is one
@@ -381,21 +385,23 @@ __global__ void __launch_bounds__(NT) k_m2l_tc(int p, int MT, uint32_t tmem_cols
 //   warps 0-7   X producers, two groups of four warps (one per tensor-memory
 //               lane quadrant) taking alternate K-chunks: the work item's 64
 //               columns, coefficients prefetched V2_D of the group's chunks
-//               ahead, split into TF32 hi/lo and written into a V2_SX-slot
-//               tensor-memory ring (A operand);
-//   warps 8-15  epilogue, two warps per lane quadrant taking alternate column
-//               slabs: accumulators -> a per-CTA scratch in global memory
-//               (L2-resident; tensor memory is free for the next item at
-//               once), then the output factors and float2 atomics into the
-//               local expansions;
+//               ahead, phase-shifted, split into three bf16 pieces and written
+//               into a V2_SX-slot tensor-memory ring (A operand);
+//   warps 8-15  epilogue, two warps per lane quadrant taking alternate row
+//               slabs: accumulators -> a per-CTA column-major scratch in global
+//               memory through a per-warp shared tile (L2-resident; tensor
+//               memory is free for the next item at once), then the output
+//               factors and float2 atomics into the local expansions, then the
+//               column data of the item two ahead;
 //   warp 16     one bulk copy per table chunk into an S_T-slot shared ring;
-//   warp 17     MMA issue: A_hi B_hi into one accumulator, A_hi B_lo + A_lo B_hi
-//               into a second (the tensor core truncates small addends against
-//               a large accumulator).
-// A chunk is V2_KS MMA K-steps of 8 real K, so that waits, fences and commits
-// are paid once per V2_KS steps; ring positions advance as counters (no
-// division in the loops).  Every wait is bounded; a wait that gives up sets
-// bit 4 of the status word and its role stops.
+//   warp 17     MMA issue, per K-step of 16 real K: X1 T1 into one accumulator,
+//               X1 T2 + X2 T1 + X1 T3 + X2 T2 + X3 T1 into a second (the tensor
+//               core truncates small addends against a large accumulator).
+// A chunk is V2_KS MMA K-steps, so that waits, fences and commits are paid
+// once per V2_KS steps; ring positions advance as counters (no division in the
+// loops).  In translation mode (M2M, L2L) the chunks run from the highest
+// input degree down.  Every wait is bounded; a wait that gives up sets bit 4
+// of the status word and its role stops.
 namespace {
 
 constexpr int V2_KS = 2;           // MMA K-steps (16 real K each) per ring chunk
