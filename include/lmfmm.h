@@ -64,15 +64,14 @@ typedef struct {
     double eta;        /* ... and its vertical transmission distance is >= eta * |c_s - c_t| */
     double quad_tol;   /* relative cut-off of the k_rho tails (>= 1e-16) */
     int precision;     /* LMFMM_FP64 or LMFMM_MIXED (FP32 translation arithmetic) */
-    int tensor_cores;  /* mixed form only: M2L products on the tcgen05 tensor cores with FP32
-                          accuracy from a three-term TF32 split.  1: the persistent kernel on a
-                          pre-tiled table image for p <= 13, else the streamed-operand kernel
-                          (p <= 15); 2: the streamed-operand kernel; 3: as 1, and M2M / L2L on
-                          the persistent kernel too (about 4x faster translations, but the
-                          tensor core's truncating accumulation compounds along the tree:
-                          2.6e-6 instead of 8e-7 on the four-layer N = 2^20, p = 12 case);
-                          0: FP32 SIMT pipes.  Beyond p = 15 the SIMT kernel runs.  Ignored by
-                          the FP64 form. */
+    int tensor_cores;  /* mixed form only: products on the tcgen05 tensor cores with FP32-level
+                          accuracy.  1: M2L on the persistent kernel (three-piece bf16 split,
+                          pre-tiled table image) for p <= 12, else the streamed-operand kernel
+                          (three-term TF32 split, p <= 15); 2: the streamed-operand kernel;
+                          3: as 1, and M2M / L2L on the persistent kernel too (inputs taken from
+                          the highest degree down; four-layer N = 2^20, p = 12: 7.3e-7 against
+                          the direct sum, 6.4e-7 with 1); 0: FP32 SIMT pipes.  Beyond p = 15 the
+                          SIMT kernel runs.  Ignored by the FP64 form. */
 } lmfmm_params;
 
 typedef struct {
@@ -86,7 +85,7 @@ typedef struct {
     int64_t n_near_pairs;  /* near box pairs */
     int64_t n_near_point_pairs;
     int64_t n_quad_nodes;  /* k_rho nodes summed over all tabulated geometries */
-    double bytes_tables;   /* device bytes held by M2L tables (or their tiled TF32 image) */
+    double bytes_tables;   /* device bytes held by M2L tables (or their tiled tensor-core image) */
     double ms_setup;       /* wall time of the last lmfmm_build */
     double ms_stage[8];    /* last matvec: P2M, M2M, M2L, L2L, L2P, S2T, permute, total */
     int64_t m2l_columns;   /* helical columns pushed through M2L tables per matvec */
