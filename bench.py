@@ -4,10 +4,13 @@ Default workload: four layers (interfaces z = 0, -1, -2, k = (1, 1.5, 2, 2.5)
 + 0.02i), N = 2^20 points in 64 Gaussian clusters (sigma 0.05) in layers 1-2,
 complex currents, truncation p = 12.  One step = one full matvec
 Phi = A J (P2M, M2M, M2L, L2L, L2P, near field) with the tree and tables
-built beforehand.  Prints one JSON line.
+built beforehand.  The mixed form runs M2L, M2M and L2L on the tensor cores
+(--tensor-cores 3); its error against the oracle's direct sum is measured on
+sampled targets in the same run.  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--precision fp64|mixed] [--workload four_layer|three_layer|two_layer]
+                  [--precision fp64|mixed] [--tensor-cores 0|1|2|3]
+                  [--workload four_layer|three_layer|two_layer|four_layer_small|three_layer_small]
 
 Multi-GPU: every rank runs an independent replica of the workload (the
 reaction components are independent FMMs, no data exchange is needed);
