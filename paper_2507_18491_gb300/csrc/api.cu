@@ -374,8 +374,8 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
     const int p = ctx->prm.p, P = (p + 1) * (p + 1);
     const int64_t N = ctx->N, nbox = (int64_t)ctx->boxes.size();
     // memory estimate (tables dominate)
-    const bool img_path = ctx->prm.precision == LMFMM_MIXED && ctx->prm.tensor_cores == 1 &&
-                          m2l_tc2_supported(p);
+    const bool img_path = ctx->prm.precision == LMFMM_MIXED &&
+                          (ctx->prm.tensor_cores == 1 || ctx->prm.tensor_cores == 3) && m2l_tc2_supported(p);
     double need = (double)ctx->geoms.size() * NTAB * P * P * 16.0 +
                   (img_path ? (double)m2l_tc2_image_bytes(p, (int64_t)ctx->geoms.size()) +
                                   (double)ctx->m2l.size() * (2 * p + 5) * 8.0

@@ -47,3 +47,9 @@ def test_bad_params_rejected_before_device_use(lib):
     prm.theta = 1.5
     assert lib.lmfmm_create(ctypes.byref(h), ctypes.byref(prm), 0) == lmfmm.ERR_ARG
     assert lib.lmfmm_create(None, ctypes.byref(prm), 0) == lmfmm.ERR_ARG
+    for bad in (-1, 4):
+        prm = lmfmm.default_params()
+        prm.precision = lmfmm.MIXED
+        prm.tensor_cores = bad
+        assert lib.lmfmm_create(ctypes.byref(h), ctypes.byref(prm), 0) == lmfmm.ERR_ARG
+        assert b"tensor_cores" in lib.lmfmm_last_error(None)
