@@ -4,8 +4,9 @@
  * horizontally layered medium (Yuan, Wang, Zhang, Cai, "Fast Multipole method
  * for Maxwell's equations in layered media", arXiv 2507.18491).
  *
- * Plain C ABI: no C++ or framework types cross it.  All complex numbers are
- * interleaved (re, im) pairs of double.  Every function returns an lmfmm_status
+ * Plain C ABI: no C++ or framework types cross it.  Complex numbers are
+ * interleaved (re, im) pairs: of double (LMFMM_C128) everywhere, and of float
+ * (LMFMM_C64) where a dtype argument allows it.  Every function returns an lmfmm_status
  * (0 = success, negative = error) unless stated otherwise; on error,
  * lmfmm_last_error() returns a one-line description for that context.
  *
@@ -43,8 +44,10 @@ typedef enum {
     LMFMM_ERR_CUDA = -2,         /* a CUDA runtime call failed */
     LMFMM_ERR_OOM = -3,          /* device allocation failed */
     LMFMM_ERR_STATE = -4,        /* calls made in the wrong order */
-    LMFMM_ERR_QUAD = -5,         /* a bounded device quadrature loop hit its cap */
-    LMFMM_ERR_UNSUPPORTED = -6   /* request outside what this build implements */
+    LMFMM_ERR_QUAD = -5,         /* a bounded quadrature hit its node cap (quad_node_cap) */
+    LMFMM_ERR_UNSUPPORTED = -6,  /* request outside what this build implements */
+    LMFMM_ERR_TIMEOUT = -7       /* a bounded device wait of the tensor-core pipeline gave up:
+                                    the result of the checked calls is invalid */
 } lmfmm_status;
 
 typedef struct lmfmm_ctx lmfmm_ctx;
@@ -55,8 +58,11 @@ typedef struct {
 
 enum { LMFMM_FP64 = 0, LMFMM_MIXED = 1 };
 
+/* element type of caller buffers of currents and fields */
+enum { LMFMM_C128 = 0, LMFMM_C64 = 1 };
+
 typedef struct {
-    int p;             /* truncation order of the expansions, 1..20 (P = (p+1)^2 coefficients) */
+    int p;             /* truncation order of the expansions, 1..16 (P = (p+1)^2 coefficients) */
     int depth;         /* octree leaf level (root = 0); < 0 selects it from leaf_cap */
     int leaf_cap;      /* target points per leaf when depth < 0 */
     double theta;      /* admissibility: box pair is far if r_s + r_t <= theta * |c_s - c_t|
@@ -72,6 +78,10 @@ typedef struct {
                           the highest degree down; four-layer N = 2^20, p = 12: 7.3e-7 against
                           the direct sum, 6.4e-7 with 1); 0: FP32 SIMT pipes.  Beyond p = 15 the
                           SIMT kernel runs.  Ignored by the FP64 form. */
+    int quad_node_cap; /* largest k_rho node count of one Sommerfeld integral (an M2L table
+                          or a near box pair); beyond it lmfmm_build returns LMFMM_ERR_QUAD
+                          (table: checked on the host before any launch; near pair: the
+                          device loop is clamped and flags it).  Default 2^20. */
 } lmfmm_params;
 
 typedef struct {
@@ -91,10 +101,20 @@ typedef struct {
     int64_t m2l_columns;   /* helical columns pushed through M2L tables per matvec */
     int m2l_kernel;        /* M2L product of the built form: 0 FP64 SIMT, 1 FP32 SIMT,
                               2 tcgen05 streamed-operand kernel, 3 tcgen05 persistent kernel */
+    int launches;          /* kernels launched by the last matvec */
+    int64_t n_geometries_same_layer;  /* of n_geometries: components with l = l' (their tables
+                                         depend on z_s - z_t only and are shared by every
+                                         pair of equal (level, rho, z_s - z_t)) */
+    double ms_tabulate;    /* last build: M2L tabulation (node factors, Chebyshev integrals,
+                              assembly), device time */
+    double tab_flops;      /* ... its arithmetic: 8 real flops per complex multiply-add of the
+                              Chebyshev integrals (80 (tau, tau', table) combinations x (p+2)
+                              degrees x (2p+3) Bessel orders per node) and of the assembly
+                              (5 P^2 (p+2) per geometry) */
 } lmfmm_stats;
 
 /* Fill *prm with defaults (p = 8, depth from leaf_cap = 64, theta = 0.55,
- * eta = 0.1, quad_tol = 1e-15, FP64, tensor_cores = 1). */
+ * eta = 0.1, quad_tol = 1e-15, FP64, tensor_cores = 1, quad_node_cap = 2^20). */
 lmfmm_status lmfmm_default_params(lmfmm_params *prm);
 
 /* Create a context on CUDA device `device`.  *out receives the handle. */
@@ -110,6 +130,11 @@ lmfmm_status lmfmm_set_layers(lmfmm_ctx *ctx, int L, const double *d, const lmfm
  * any previous build. */
 lmfmm_status lmfmm_set_points(lmfmm_ctx *ctx, int64_t N, const double *xyz);
 
+/* The same with xyz[N][3] in DEVICE memory, read in order on `stream`; the
+ * tree is built on the host, so the call copies the points back and returns
+ * after the copy (the caller may free or overwrite xyz afterwards). */
+lmfmm_status lmfmm_set_points_device(lmfmm_ctx *ctx, int64_t N, const double *xyz, void *stream);
+
 /* Setup: per-layer octrees, dual-tree traversal of every reaction component
  * into far (M2L) and near (direct) box pairs, deduplication of M2L
  * geometries, device tabulation of the M2L Sommerfeld integrals (Section 3.4)
@@ -117,20 +142,36 @@ lmfmm_status lmfmm_set_points(lmfmm_ctx *ctx, int64_t N, const double *xyz);
 lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream);
 
 /* Phi = A J with A the reaction-field operator above.  J[N][3] and Phi[N][3]
- * are DEVICE pointers to complex doubles in the caller's point order; Phi is
- * overwritten.  Asynchronous on `stream`. */
-lmfmm_status lmfmm_matvec(lmfmm_ctx *ctx, const lmfmm_c128 *J, lmfmm_c128 *Phi, void *stream);
+ * are DEVICE pointers in the caller's point order, both of element type
+ * `dtype` (LMFMM_C128 or LMFMM_C64; complex64 currents are widened exactly and
+ * the complex128 sum is rounded once into a complex64 Phi); Phi is
+ * overwritten.  Asynchronous on `stream`: argument and state errors are
+ * returned at once, while a device-side failure (LMFMM_ERR_TIMEOUT) is
+ * reported by lmfmm_check after the call has run. */
+lmfmm_status lmfmm_matvec(lmfmm_ctx *ctx, const void *J, int dtype, void *Phi, void *stream);
 
-/* Same operator with HOST buffers J[N][3], Phi[N][3]: copies in, applies,
- * copies out; returns after Phi is written.  Pinned host memory is faster. */
-lmfmm_status lmfmm_matvec_host(lmfmm_ctx *ctx, const lmfmm_c128 *J, lmfmm_c128 *Phi,
-                               void *stream);
+/* Same operator with HOST buffers J[N][3], Phi[N][3] of element type dtype:
+ * copies in, applies, copies out; returns after Phi is written, with the
+ * device status checked (lmfmm_check).  Pinned host memory is faster. */
+lmfmm_status lmfmm_matvec_host(lmfmm_ctx *ctx, const void *J, int dtype, void *Phi, void *stream);
 
-/* Phi = A^H y (device buffers).  The reaction operator is complex symmetric
- * (reciprocity, G(r,r') = G(r',r)^T, which the paper invokes for summing over
- * the first slot), so A^H y = conj(A conj(y)); this applies exactly that. */
-lmfmm_status lmfmm_matvec_adjoint(lmfmm_ctx *ctx, const lmfmm_c128 *y, lmfmm_c128 *Phi,
+/* Phi = A^H y (device buffers of element type dtype).  The reaction operator
+ * is complex symmetric (reciprocity, G(r,r') = G(r',r)^T, which the paper
+ * invokes for summing over the first slot), so A^H y = conj(A conj(y)); this
+ * applies exactly that.  Asynchronous like lmfmm_matvec. */
+lmfmm_status lmfmm_matvec_adjoint(lmfmm_ctx *ctx, const void *y, int dtype, void *Phi,
                                   void *stream);
+
+/* Waits for `stream` and reads the context's device status word, which every
+ * matvec clears (stream-ordered) before its first kernel.  Returns LMFMM_OK,
+ * LMFMM_ERR_TIMEOUT if a bounded wait inside a tensor-core kernel of the
+ * matvecs since then gave up (that result is incomplete), or LMFMM_ERR_CUDA. */
+lmfmm_status lmfmm_check(lmfmm_ctx *ctx, void *stream);
+
+/* Test hook for the error path above: ORs `bits` into the device status word
+ * from the host (synchronous), as a tensor-core wait that gives up would.
+ * Bit 4 is the only meaning defined today.  Requires lmfmm_build. */
+lmfmm_status lmfmm_test_set_status(lmfmm_ctx *ctx, int bits);
 
 /* Direct evaluation of the same operator over ALL point pairs with the
  * device near-field kernel (Sommerfeld integral per pair, Section 3.5);
@@ -151,9 +192,11 @@ lmfmm_status lmfmm_direct(lmfmm_ctx *ctx, const lmfmm_c128 *J, lmfmm_c128 *Phi, 
  * (leaf pairs * 48 bytes, rounded up to 256) + (point pairs * 80 bytes)
  * exceeds 32 MiB -- about N^2 <= 4e5 point pairs over all components.
  * The array is shared by every call on a device and keeps the last call's
- * contents; the call zero-fills what must start at zero.  Calls that
- * overlap on the GPU (other streams, other contexts on the same device)
- * race on it.  The first call on each device looks up the array's device
+ * contents; the call zero-fills what must start at zero.  The array, the
+ * host pair list and the per-device address cache are process-wide, so the
+ * call holds a process-wide lock from the pair list to its final wait: calls
+ * from several host threads (any contexts, any devices) run one at a time
+ * and never overlap on the GPU.  The first call on each device looks up the array's device
  * address (cudaGetSymbolAddress) with that device current; make that first
  * call before any stream capture.  J, Phi: DEVICE [N][3] complex, caller's
  * point order; synchronous (returns after Phi is written). */

@@ -126,13 +126,6 @@ lmfmm_status dupload(lmfmm_ctx *ctx, T **p, const std::vector<T> &h)
         if (s_ != LMFMM_OK) return s_; \
     } while (0)
 
-double medium_a(const MediumDev &M)
-{
-    double km = 0;
-    for (int j = 0; j <= M.L; ++j) km = std::max(km, std::hypot(M.k[j].x, M.k[j].y));
-    return 1.5 * km + 0.75;
-}
-
 // k_rho quadrature plan of an M2L geometry: the Chebyshev integrands carry
 // a polynomial of degree up to 2p+5 in k_rho.
 QuadPlanDev geom_plan(double a, int p, double rho, double dz) { return make_plan(a, rho, dz, 2 * p + 5); }
@@ -148,15 +141,18 @@ lmfmm_status check_flag(lmfmm_ctx *ctx)
     return LMFMM_OK;
 }
 
-// Status word of the matvec kernels (sticky until the next build): a
-// tensor-core wait that gave up leaves bit 4.
-lmfmm_status check_mvstatus(lmfmm_ctx *ctx)
+// Status word of the matvec kernels, cleared by every matvec before its first
+// kernel: a tensor-core wait that gave up leaves bit 4.  Reads it after the
+// stream's work is done.
+lmfmm_status check_mvstatus(lmfmm_ctx *ctx, cudaStream_t st)
 {
     int f = 0;
+    CK(cudaStreamSynchronize(st));
     CK(cudaMemcpy(&f, DS(ctx)->mvstatus, sizeof(int), cudaMemcpyDeviceToHost));
     if (f) {
-        ctx->err = "matvec: a tensor-core wait gave up (status " + std::to_string(f) + ")";
-        return LMFMM_ERR_CUDA;
+        ctx->err = "matvec: a bounded tensor-core wait gave up (status " + std::to_string(f) +
+                   "); the result is incomplete";
+        return LMFMM_ERR_TIMEOUT;
     }
     return LMFMM_OK;
 }
@@ -164,7 +160,7 @@ lmfmm_status check_mvstatus(lmfmm_ctx *ctx)
 // Tabulate a list of geometries into `tab` (device), batching node factors
 // and Chebyshev integrals through a scratch buffer.
 lmfmm_status tabulate(lmfmm_ctx *ctx, std::vector<GeomDev> &hg, const CompDev *dcomps,
-                      const cd *dG, const int *dcg, cd *tab, cudaStream_t st)
+                      const cd *dG, const int *dcg, cd *tab, cudaStream_t st, float *ms = nullptr)
 {
     const int p = ctx->prm.p;
     const int LM = p + 2, DJ = 2 * p + 3;
@@ -214,6 +210,9 @@ lmfmm_status tabulate(lmfmm_ctx *ctx, std::vector<GeomDev> &hg, const CompDev *d
     if (!hg.empty() &&
         cudaMemcpy(dgeo, hg.data(), hg.size() * sizeof(GeomDev), cudaMemcpyHostToDevice))
         rc = LMFMM_ERR_CUDA;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    const bool timed = ms && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
+    if (timed) cudaEventRecord(e0, st);
     for (size_t b = 0; rc == LMFMM_OK && b + 1 < bstart.size(); ++b) {
         int g0 = bstart[b], nb = bstart[b + 1] - g0;
         int qmax = 0;
@@ -222,7 +221,13 @@ lmfmm_status tabulate(lmfmm_ctx *ctx, std::vector<GeomDev> &hg, const CompDev *d
                          DS(ctx)->flag, st);
         if (cudaGetLastError() != cudaSuccess) rc = LMFMM_ERR_CUDA;
     }
+    if (timed) cudaEventRecord(e1, st);
     if (cudaStreamSynchronize(st) != cudaSuccess) rc = LMFMM_ERR_CUDA;
+    if (timed) {
+        if (cudaEventElapsedTime(ms, e0, e1) != cudaSuccess) *ms = 0.f;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
     cudaFree(qg);
     cudaFree(qs);
     if (rc) {
@@ -267,6 +272,7 @@ lmfmm_status lmfmm_default_params(lmfmm_params *prm)
     prm->quad_tol = 1e-15;
     prm->precision = LMFMM_FP64;
     prm->tensor_cores = 1;
+    prm->quad_node_cap = 1 << 20;
     return LMFMM_OK;
 }
 
@@ -289,6 +295,10 @@ lmfmm_status lmfmm_create(lmfmm_ctx **out, const lmfmm_params *prm, int device)
     }
     if (prm->tensor_cores < 0 || prm->tensor_cores > 3) {
         g_err = "lmfmm_create: tensor_cores must be 0, 1, 2 or 3";
+        return LMFMM_ERR_ARG;
+    }
+    if (prm->quad_node_cap < 64) {
+        g_err = "lmfmm_create: quad_node_cap must be at least 64";
         return LMFMM_ERR_ARG;
     }
     cudaError_t e = cudaSetDevice(device);
@@ -353,6 +363,21 @@ lmfmm_status lmfmm_set_points(lmfmm_ctx *ctx, int64_t N, const double *xyz)
     lmfmm_status s = classify_and_sort(ctx);
     ctx->points_set = (s == LMFMM_OK);
     return s;
+}
+
+lmfmm_status lmfmm_set_points_device(lmfmm_ctx *ctx, int64_t N, const double *xyz, void *stream)
+{
+    if (!ctx) return LMFMM_ERR_ARG;
+    if (N < 1 || !xyz) {
+        ctx->err = "set_points_device: need N >= 1 and a non-NULL array";
+        return LMFMM_ERR_ARG;
+    }
+    CK(cudaSetDevice(ctx->device));
+    std::vector<double> h((size_t)N * 3);
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(h.data(), xyz, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return lmfmm_set_points(ctx, N, h.data());
 }
 
 lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
@@ -438,6 +463,7 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
     const double a = medium_a(ctx->med);
     std::vector<GeomDev> hg(ctx->geoms.size());
     int64_t qtot = 0;
+    float ms_tab = 0.f;
     for (size_t i = 0; i < ctx->geoms.size(); ++i) {
         const Geom &g = ctx->geoms[i];
         const CompDev &c = ctx->comps[g.comp];
@@ -451,8 +477,9 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
         gd.plan = geom_plan(a, p, g.rho, c.s * (g.zs - g.zt));
         gd.scale_s = kabs(c.l) * lev_size(g.level);
         gd.scale_t = kabs(c.lp) * lev_size(g.level);
-        if (plan_nodes(gd.plan) > (1 << 20)) {
-            ctx->err = "build: an M2L geometry needs more than 2^20 quadrature nodes";
+        if (plan_nodes(gd.plan) > ctx->prm.quad_node_cap) {
+            ctx->err = "build: an M2L geometry needs " + std::to_string(plan_nodes(gd.plan)) +
+                       " quadrature nodes, more than quad_node_cap = " + std::to_string(ctx->prm.quad_node_cap);
             return LMFMM_ERR_QUAD;
         }
         qtot += plan_nodes(gd.plan);
@@ -463,7 +490,7 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
         // FP64 Chebyshev tabulation, then level scaling (and cast for the mixed form)
         cd *tab64 = nullptr;
         TRY(dalloc(ctx, &tab64, ctx->geoms.size() * (size_t)NTAB * P * P));
-        TRY(tabulate(ctx, hg, d->comps, dG, dcg, tab64, st));
+        TRY(tabulate(ctx, hg, d->comps, dG, dcg, tab64, st, &ms_tab));
         TRY(dupload(ctx, &d->geoms, hg));
         if (d->m2l_kernel == 3) {
             unsigned char *img = nullptr;
@@ -635,7 +662,7 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
         cd *s2t5 = nullptr;
         TRY(dalloc(ctx, &s2t5, (size_t)ctx->n_near_pp * 5));
         launch_s2t_pre((int64_t)ctx->near.size(), d->near, d->boxes, d->xyz, ctx->med, d->comps, a,
-                       0.5 * a, s2t5, d->flag, st);
+                       ctx->prm.quad_node_cap, s2t5, d->flag, st);
         CK(cudaGetLastError());
         TRY(dalloc(ctx, &d->s2t, (size_t)ctx->n_near_pp * 8));
         launch_s2t_combine((int64_t)ctx->near.size(), d->near, d->boxes, d->xyz, s2t5, d->s2t, st);
@@ -672,12 +699,17 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
     S.ms_setup = std::chrono::duration<double, std::milli>(t1 - t0).count();
     S.m2l_columns = ncols;
     S.m2l_kernel = d->m2l_kernel;
+    for (const Geom &g : ctx->geoms)
+        if (ctx->comps[g.comp].l == ctx->comps[g.comp].lp) ++S.n_geometries_same_layer;
+    S.ms_tabulate = ms_tab;
+    S.tab_flops = 8.0 * (double)qtot * NTAB * 16 * (p + 2) * (2 * p + 3) +
+                  8.0 * (double)ctx->geoms.size() * NTAB * (double)P * P * (p + 2);
     return LMFMM_OK;
 }
 
 extern "C++" {
 template <typename T>
-static lmfmm_status matvec_t(lmfmm_ctx *ctx, const lmfmm_c128 *J, lmfmm_c128 *Phi,
+static lmfmm_status matvec_t(lmfmm_ctx *ctx, const void *J, int dtype, void *Phi,
                              cudaStream_t st, bool cj)
 {
     DevState *d = DS(ctx);
@@ -685,8 +717,12 @@ static lmfmm_status matvec_t(lmfmm_ctx *ctx, const lmfmm_c128 *J, lmfmm_c128 *Ph
     const int64_t N = ctx->N, nbox = (int64_t)ctx->boxes.size();
     cx<T> *me = (cx<T> *)d->me, *le = (cx<T> *)d->le;
     const cx<T> *tup = (const cx<T> *)d->tup, *tdn = (const cx<T> *)d->tdn;
+    int nl = 0;   // kernels launched (launchers skip empty work)
     CK(cudaEventRecord(d->ev[0], st));
-    launch_gather_in(N, d->perm, (const cd *)J, d->qh, cj, st);
+    CK(cudaMemsetAsync(d->mvstatus, 0, sizeof(int), st));
+    launch_gather_in(N, d->perm, J, dtype, d->qh, cj, st);
+    nl += N > 0;
+    nl += d->nleaves > 0;   // P2M
     CK(cudaMemsetAsync(me, 0, (size_t)nbox * 3 * P * sizeof(cx<T>), st));
     launch_p2m<T>(p, d->nleaves, d->leaves, d->boxes, d->xyz, d->qh, ctx->med, d->lscale, me, st);
     CK(cudaEventRecord(d->ev[1], st));
@@ -696,13 +732,16 @@ static lmfmm_status matvec_t(lmfmm_ctx *ctx, const lmfmm_c128 *J, lmfmm_c128 *Ph
                 int64_t w0 = d->twork_off[lev], w1 = d->twork_off[lev + 1];
                 CK(launch_trans_tc2(p, w1 - w0, d->twork + w0, d->tchild, d->tparent, d->tupi, me, me,
                                     d->yscr, d->nsm, d->mvstatus, st));
+                nl += w1 > w0;
                 continue;
             }
         }
         int64_t w0 = d->gwork_off[lev], w1 = d->gwork_off[lev + 1];
         launch_group_gemm_t<T>(p, w1 - w0, d->gwork + w0, tup, d->tchild, d->tparent, me, me, true,
                                st);
+        nl += w1 > w0;
     }
+    nl += d->n_m2lwork > 0;   // M2L
     CK(cudaEventRecord(d->ev[2], st));
     CK(cudaMemsetAsync(le, 0, (size_t)nbox * 3 * P * sizeof(cx<T>), st));
     if constexpr (std::is_same<T, float>::value) {
@@ -727,6 +766,7 @@ static lmfmm_status matvec_t(lmfmm_ctx *ctx, const lmfmm_c128 *J, lmfmm_c128 *Ph
                 int64_t w0 = d->twork_off[lev], w1 = d->twork_off[lev + 1];
                 CK(launch_trans_tc2(p, w1 - w0, d->twork + w0, d->tparent, d->tchild, d->tdni, le, le,
                                     d->yscr, d->nsm, d->mvstatus, st));
+                nl += w1 > w0;
                 continue;
             }
         }
@@ -734,80 +774,105 @@ static lmfmm_status matvec_t(lmfmm_ctx *ctx, const lmfmm_c128 *J, lmfmm_c128 *Ph
         // a child has one parent: reductions (fire and forget) rather than read-modify-write
         launch_group_gemm_t<T>(p, w1 - w0, d->gwork + w0, tdn, d->tparent, d->tchild, le, le, true,
                                st);
+        nl += w1 > w0;
     }
     CK(cudaEventRecord(d->ev[4], st));
     launch_l2p<T>(p, d->nleaves, d->leaves, d->boxes, d->xyz, le, ctx->med, d->lscale, d->ph, st);
     CK(cudaEventRecord(d->ev[5], st));
     launch_s2t_apply8(d->n_s2twork, d->s2twork, d->near, d->boxes, d->s2t, d->qh, d->ph, st);
     CK(cudaEventRecord(d->ev[6], st));
-    launch_scatter_out(N, d->perm, d->ph, (cd *)Phi, cj, st);
+    launch_scatter_out(N, d->perm, d->ph, Phi, dtype, cj, st);
+    nl += (d->nleaves > 0) + (d->n_s2twork > 0) + (N > 0);   // L2P, near field, scatter
     CK(cudaEventRecord(d->ev[7], st));
     CK(cudaGetLastError());
     d->mv_recorded = true;
+    ctx->stats.launches = nl;
     return LMFMM_OK;
 }
 
-static lmfmm_status matvec_impl(lmfmm_ctx *ctx, const lmfmm_c128 *J, lmfmm_c128 *Phi,
+static lmfmm_status matvec_impl(lmfmm_ctx *ctx, const void *J, int dtype, void *Phi,
                                 cudaStream_t st, bool cj)
 {
-    if (ctx->prm.precision == LMFMM_MIXED) return matvec_t<float>(ctx, J, Phi, st, cj);
-    return matvec_t<double>(ctx, J, Phi, st, cj);
+    if (ctx->prm.precision == LMFMM_MIXED) return matvec_t<float>(ctx, J, dtype, Phi, st, cj);
+    return matvec_t<double>(ctx, J, dtype, Phi, st, cj);
 }
 }  // extern "C++"
 
-lmfmm_status lmfmm_matvec(lmfmm_ctx *ctx, const lmfmm_c128 *J, lmfmm_c128 *Phi, void *stream)
+static lmfmm_status matvec_args(lmfmm_ctx *ctx, const char *who, const void *J, int dtype, const void *Phi)
 {
-    if (!ctx) return LMFMM_ERR_ARG;
     if (!ctx->built) {
-        ctx->err = "matvec: call lmfmm_build first";
+        ctx->err = std::string(who) + ": call lmfmm_build first";
         return LMFMM_ERR_STATE;
     }
     if (!J || !Phi) {
-        ctx->err = "matvec: NULL buffer";
+        ctx->err = std::string(who) + ": NULL buffer";
         return LMFMM_ERR_ARG;
     }
-    CK(cudaSetDevice(ctx->device));
-    return matvec_impl(ctx, J, Phi, (cudaStream_t)stream, false);
+    if (dtype != LMFMM_C128 && dtype != LMFMM_C64) {
+        ctx->err = std::string(who) + ": dtype must be LMFMM_C128 or LMFMM_C64";
+        return LMFMM_ERR_ARG;
+    }
+    return LMFMM_OK;
 }
 
-lmfmm_status lmfmm_matvec_adjoint(lmfmm_ctx *ctx, const lmfmm_c128 *y, lmfmm_c128 *Phi,
-                                  void *stream)
+lmfmm_status lmfmm_matvec(lmfmm_ctx *ctx, const void *J, int dtype, void *Phi, void *stream)
 {
     if (!ctx) return LMFMM_ERR_ARG;
-    if (!ctx->built) {
-        ctx->err = "matvec_adjoint: call lmfmm_build first";
-        return LMFMM_ERR_STATE;
-    }
-    if (!y || !Phi) {
-        ctx->err = "matvec_adjoint: NULL buffer";
-        return LMFMM_ERR_ARG;
-    }
+    TRY(matvec_args(ctx, "matvec", J, dtype, Phi));
     CK(cudaSetDevice(ctx->device));
-    return matvec_impl(ctx, y, Phi, (cudaStream_t)stream, true);
+    return matvec_impl(ctx, J, dtype, Phi, (cudaStream_t)stream, false);
 }
 
-lmfmm_status lmfmm_matvec_host(lmfmm_ctx *ctx, const lmfmm_c128 *J, lmfmm_c128 *Phi, void *stream)
+lmfmm_status lmfmm_matvec_adjoint(lmfmm_ctx *ctx, const void *y, int dtype, void *Phi, void *stream)
 {
     if (!ctx) return LMFMM_ERR_ARG;
-    if (!ctx->built) {
-        ctx->err = "matvec_host: call lmfmm_build first";
-        return LMFMM_ERR_STATE;
-    }
-    if (!J || !Phi) {
-        ctx->err = "matvec_host: NULL buffer";
-        return LMFMM_ERR_ARG;
-    }
+    TRY(matvec_args(ctx, "matvec_adjoint", y, dtype, Phi));
+    CK(cudaSetDevice(ctx->device));
+    return matvec_impl(ctx, y, dtype, Phi, (cudaStream_t)stream, true);
+}
+
+lmfmm_status lmfmm_matvec_host(lmfmm_ctx *ctx, const void *J, int dtype, void *Phi, void *stream)
+{
+    if (!ctx) return LMFMM_ERR_ARG;
+    TRY(matvec_args(ctx, "matvec_host", J, dtype, Phi));
     CK(cudaSetDevice(ctx->device));
     DevState *d = DS(ctx);
     cudaStream_t st = (cudaStream_t)stream;
-    const size_t bytes = (size_t)ctx->N * 3 * sizeof(cd);
+    const size_t bytes = (size_t)ctx->N * 3 * (dtype == LMFMM_C64 ? sizeof(cf) : sizeof(cd));
+    // staging [2][N][3] complex128, used at the caller's element size
     if (!d->stage) TRY(dalloc(ctx, &d->stage, (size_t)ctx->N * 6));
-    CK(cudaMemcpyAsync(d->stage, J, bytes, cudaMemcpyHostToDevice, st));
-    TRY(matvec_impl(ctx, (const lmfmm_c128 *)d->stage, (lmfmm_c128 *)(d->stage + 3 * ctx->N), st,
-                    false));
-    CK(cudaMemcpyAsync(Phi, d->stage + 3 * ctx->N, bytes, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    return check_mvstatus(ctx);
+    unsigned char *sin = (unsigned char *)d->stage, *sout = (unsigned char *)(d->stage + 3 * ctx->N);
+    CK(cudaMemcpyAsync(sin, J, bytes, cudaMemcpyHostToDevice, st));
+    TRY(matvec_impl(ctx, sin, dtype, sout, st, false));
+    CK(cudaMemcpyAsync(Phi, sout, bytes, cudaMemcpyDeviceToHost, st));
+    return check_mvstatus(ctx, st);
+}
+
+lmfmm_status lmfmm_check(lmfmm_ctx *ctx, void *stream)
+{
+    if (!ctx) return LMFMM_ERR_ARG;
+    if (!ctx->built || !DS(ctx) || !DS(ctx)->mvstatus) {
+        ctx->err = "check: call lmfmm_build first";
+        return LMFMM_ERR_STATE;
+    }
+    CK(cudaSetDevice(ctx->device));
+    return check_mvstatus(ctx, (cudaStream_t)stream);
+}
+
+lmfmm_status lmfmm_test_set_status(lmfmm_ctx *ctx, int bits)
+{
+    if (!ctx) return LMFMM_ERR_ARG;
+    if (!ctx->built || !DS(ctx) || !DS(ctx)->mvstatus) {
+        ctx->err = "test_set_status: call lmfmm_build first";
+        return LMFMM_ERR_STATE;
+    }
+    CK(cudaSetDevice(ctx->device));
+    int f = 0;
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(&f, DS(ctx)->mvstatus, sizeof(int), cudaMemcpyDeviceToHost));
+    f |= bits;
+    CK(cudaMemcpy(DS(ctx)->mvstatus, &f, sizeof(int), cudaMemcpyHostToDevice));
+    return LMFMM_OK;
 }
 
 lmfmm_status lmfmm_direct(lmfmm_ctx *ctx, const lmfmm_c128 *J, lmfmm_c128 *Phi, void *stream)
@@ -825,48 +890,12 @@ lmfmm_status lmfmm_direct(lmfmm_ctx *ctx, const lmfmm_c128 *J, lmfmm_c128 *Phi, 
     DevState *d = DS(ctx);
     cudaStream_t st = (cudaStream_t)stream;
     // every (component, source leaf, target leaf) pair is treated as near
-    std::vector<NearPair> all;
-    int64_t npp = 0;
-    for (int ci = 0; ci < (int)ctx->comps.size(); ++ci) {
-        const CompDev &c = ctx->comps[ci];
-        int D = ctx->depth;
-        for (int64_t bs = ctx->lvl0[c.l][D]; bs < ctx->lvl1[c.l][D]; ++bs)
-            for (int64_t bt = ctx->lvl0[c.lp][D]; bt < ctx->lvl1[c.lp][D]; ++bt) {
-                const Box &B = ctx->boxes[bs], &C = ctx->boxes[bt];
-                double smn = 1e300, smx = -1e300, tmn = 1e300, tmx = -1e300;
-                double bl[2] = {1e300, 1e300}, bh[2] = {-1e300, -1e300}, cl[2] = {1e300, 1e300},
-                       ch[2] = {-1e300, -1e300};
-                for (int64_t t = B.p0; t < B.p1; ++t) {
-                    double z = comp_src_z(c, ctx->sxyz[3 * t + 2]);
-                    smn = std::min(smn, z);
-                    smx = std::max(smx, z);
-                    for (int e = 0; e < 2; ++e) {
-                        bl[e] = std::min(bl[e], ctx->sxyz[3 * t + e]);
-                        bh[e] = std::max(bh[e], ctx->sxyz[3 * t + e]);
-                    }
-                }
-                for (int64_t t = C.p0; t < C.p1; ++t) {
-                    double z = comp_tgt_z(c, ctx->sxyz[3 * t + 2]);
-                    tmn = std::min(tmn, z);
-                    tmx = std::max(tmx, z);
-                    for (int e = 0; e < 2; ++e) {
-                        cl[e] = std::min(cl[e], ctx->sxyz[3 * t + e]);
-                        ch[e] = std::max(ch[e], ctx->sxyz[3 * t + e]);
-                    }
-                }
-                NearPair np{};
-                np.comp = ci;
-                np.src = bs;
-                np.tgt = bt;
-                np.coef0 = npp;
-                np.dzmin = c.s > 0 ? smn - tmx : tmn - smx;
-                double mx = std::max(std::fabs(bh[0] - cl[0]), std::fabs(ch[0] - bl[0]));
-                double my = std::max(std::fabs(bh[1] - cl[1]), std::fabs(ch[1] - bl[1]));
-                np.rhomax = std::sqrt(mx * mx + my * my);
-                npp += (B.p1 - B.p0) * (C.p1 - C.p0);
-                all.push_back(np);
-            }
-    }
+    int64_t npp = 0, cnt = 0;
+    for (const CompDev &c : ctx->comps)
+        cnt += (ctx->lvl1[c.l][ctx->depth] - ctx->lvl0[c.l][ctx->depth]) *
+               (ctx->lvl1[c.lp][ctx->depth] - ctx->lvl0[c.lp][ctx->depth]);
+    std::vector<NearPair> all((size_t)cnt);
+    all_leaf_pairs(ctx, all.data(), cnt, &npp);
     NearPair *dn = nullptr;
     cd *coef = nullptr;
     void *q1 = nullptr, *q2 = nullptr;
@@ -884,12 +913,13 @@ lmfmm_status lmfmm_direct(lmfmm_ctx *ctx, const lmfmm_c128 *J, lmfmm_c128 *Phi, 
         rc = LMFMM_ERR_CUDA;
     if (!rc) {
         double a = medium_a(ctx->med);
-        launch_gather_in(ctx->N, d->perm, (const cd *)J, d->qh, false, st);
+        cudaMemsetAsync(d->flag, 0, sizeof(int), st);
+        launch_gather_in(ctx->N, d->perm, J, LMFMM_C128, d->qh, false, st);
         cudaMemsetAsync(d->ph, 0, (size_t)ctx->N * 3 * sizeof(cd), st);
-        launch_s2t_pre((int64_t)all.size(), dn, d->boxes, d->xyz, ctx->med, d->comps, a, 0.5 * a,
-                       coef, d->flag, st);
+        launch_s2t_pre((int64_t)all.size(), dn, d->boxes, d->xyz, ctx->med, d->comps, a,
+                       ctx->prm.quad_node_cap, coef, d->flag, st);
         launch_s2t_apply((int64_t)all.size(), dn, d->boxes, d->xyz, coef, d->qh, d->ph, st);
-        launch_scatter_out(ctx->N, d->perm, d->ph, (cd *)Phi, false, st);
+        launch_scatter_out(ctx->N, d->perm, d->ph, Phi, LMFMM_C128, false, st);
         if (cudaStreamSynchronize(st) != cudaSuccess) rc = LMFMM_ERR_CUDA;
     }
     cudaFree(q1);

@@ -349,6 +349,39 @@ lmfmm_status build_host_structures(lmfmm_ctx *ctx)
     return LMFMM_OK;
 }
 
+int64_t all_leaf_pairs(const lmfmm_ctx *ctx, NearPair *out, int64_t cap, int64_t *npp_out)
+{
+    int64_t np = 0, npp = 0;
+    const int D = ctx->depth;
+    for (int ci = 0; ci < (int)ctx->comps.size(); ++ci) {
+        const CompDev &c = ctx->comps[ci];
+        for (int64_t bs = ctx->lvl0[c.l][D]; bs < ctx->lvl1[c.l][D]; ++bs)
+            for (int64_t bt = ctx->lvl0[c.lp][D]; bt < ctx->lvl1[c.lp][D]; ++bt) {
+                if (np >= cap) return -1;
+                const Box &B = ctx->boxes[bs], &C = ctx->boxes[bt];
+                double smx, tmx;
+                const double smn = box_min_mapped(ctx, B, c, true, &smx);
+                const double tmn = box_min_mapped(ctx, C, c, false, &tmx);
+                double blo[2], bhi[2], clo[2], chi[2];
+                box_xy_extent(ctx, B, blo, bhi);
+                box_xy_extent(ctx, C, clo, chi);
+                NearPair q{};
+                q.comp = ci;
+                q.src = bs;
+                q.tgt = bt;
+                q.coef0 = npp;
+                q.dzmin = c.s > 0 ? smn - tmx : tmn - smx;
+                const double mx = std::max(std::fabs(bhi[0] - clo[0]), std::fabs(chi[0] - blo[0]));
+                const double my = std::max(std::fabs(bhi[1] - clo[1]), std::fabs(chi[1] - blo[1]));
+                q.rhomax = std::sqrt(mx * mx + my * my);
+                out[np++] = q;
+                npp += (B.p1 - B.p0) * (C.p1 - C.p0);
+            }
+    }
+    *npp_out = npp;
+    return np;
+}
+
 // ---------------------------------------------------------------- Chebyshev
 
 typedef long double ld;

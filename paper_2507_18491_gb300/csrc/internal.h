@@ -1,5 +1,7 @@
 // Internal declarations shared by the host setup code and the CUDA kernels.
 #pragma once
+#include <algorithm>
+#include <cmath>
 #include <complex>
 #include <cstdint>
 #include <string>
@@ -122,8 +124,22 @@ struct lmfmm_ctx {
 };
 
 namespace lmf {
+// End point a of the contour Gamma_1 (Section 3.5): beyond every layer wavenumber.
+inline double medium_a(const MediumDev &M)
+{
+    double km = 0;
+    for (int j = 0; j <= M.L; ++j) km = std::max(km, std::hypot(M.k[j].x, M.k[j].y));
+    return 1.5 * km + 0.75;
+}
+
 // host_setup.cpp
 lmfmm_status build_host_structures(lmfmm_ctx *ctx);
+// Every (component, source leaf, target leaf) pair of the context as a near
+// pair (the all-pairs direct evaluation), written to out[0 .. cap); returns the
+// number of pairs, or -1 if there are more than cap (nothing past cap is
+// written).  *npp receives the point-pair count, the pairs' coefficient
+// offsets (coef0) run over it.
+int64_t all_leaf_pairs(const lmfmm_ctx *ctx, NearPair *out, int64_t cap, int64_t *npp);
 void chebyshev_tables(lmfmm_ctx *ctx);
 void bcoef_table(int p, int KMAX, std::vector<double> &B);
 void gtensor(int p, const std::vector<double> &Bcoef, int KM, zc k, zc kp, cd *dst);

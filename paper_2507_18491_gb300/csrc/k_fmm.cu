@@ -8,21 +8,29 @@ namespace lmf {
 
 
 // ------------------------------------------------------------ permutation
+// Caller buffers are complex128 or complex64 [N][3]; the helical work arrays
+// are complex128 in sorted order.
+template <typename TI>
+__device__ __forceinline__ cd load_c(const TI *p) { return cd{(double)p->x, (double)p->y}; }
+
 // q_h[i] = (J_x + i J_y, J_x - i J_y, J_z) of point perm[i] (optionally of conj J)
-__global__ void k_gather_in(int64_t N, const int64_t *perm, const cd *J, cd *qh, int cj)
+template <typename TI>
+__global__ void k_gather_in(int64_t N, const int64_t *perm, const TI *J, cd *qh, int cj)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= N) return;
     int64_t o = perm[i];
-    cd x = J[3 * o], y = J[3 * o + 1], z = J[3 * o + 2];
+    cd x = load_c(J + 3 * o), y = load_c(J + 3 * o + 1), z = load_c(J + 3 * o + 2);
     if (cj) { x = conj(x); y = conj(y); z = conj(z); }
     qh[3 * i] = x + mul_i(y);
     qh[3 * i + 1] = x - mul_i(y);
     qh[3 * i + 2] = z;
 }
 
-// Phi[perm[i]] = ((A+B)/2, (A-B)/(2i), C) of the helical result (optionally conj)
-__global__ void k_scatter_out(int64_t N, const int64_t *perm, const cd *ph, cd *Phi, int cj)
+// Phi[perm[i]] = ((A+B)/2, (A-B)/(2i), C) of the helical result (optionally conj);
+// the complex64 output is rounded once from the complex128 sum
+template <typename TO>
+__global__ void k_scatter_out(int64_t N, const int64_t *perm, const cd *ph, TO *Phi, int cj)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= N) return;
@@ -30,21 +38,31 @@ __global__ void k_scatter_out(int64_t N, const int64_t *perm, const cd *ph, cd *
     cd A = ph[3 * i], B = ph[3 * i + 1], C = ph[3 * i + 2];
     cd x = 0.5 * (A + B), y = mul_mi(0.5 * (A - B));
     if (cj) { x = conj(x); y = conj(y); C = conj(C); }
-    Phi[3 * o] = x;
-    Phi[3 * o + 1] = y;
-    Phi[3 * o + 2] = C;
+    using E = decltype(Phi->x);
+    Phi[3 * o] = TO{(E)x.x, (E)x.y};
+    Phi[3 * o + 1] = TO{(E)y.x, (E)y.y};
+    Phi[3 * o + 2] = TO{(E)C.x, (E)C.y};
 }
 
-void launch_gather_in(int64_t N, const int64_t *perm, const cd *J, cd *qh, bool conj_in,
+void launch_gather_in(int64_t N, const int64_t *perm, const void *J, int dtype, cd *qh, bool conj_in,
                       cudaStream_t st)
 {
-    if (N > 0) k_gather_in<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, perm, J, qh, conj_in);
+    if (N <= 0) return;
+    const unsigned g = (unsigned)((N + 255) / 256);
+    if (dtype == LMFMM_C64)
+        k_gather_in<cf><<<g, 256, 0, st>>>(N, perm, (const cf *)J, qh, conj_in);
+    else
+        k_gather_in<cd><<<g, 256, 0, st>>>(N, perm, (const cd *)J, qh, conj_in);
 }
-void launch_scatter_out(int64_t N, const int64_t *perm, const cd *phih, cd *Phi, bool conj_out,
+void launch_scatter_out(int64_t N, const int64_t *perm, const cd *phih, void *Phi, int dtype, bool conj_out,
                         cudaStream_t st)
 {
-    if (N > 0)
-        k_scatter_out<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, perm, phih, Phi, conj_out);
+    if (N <= 0) return;
+    const unsigned g = (unsigned)((N + 255) / 256);
+    if (dtype == LMFMM_C64)
+        k_scatter_out<cf><<<g, 256, 0, st>>>(N, perm, phih, (cf *)Phi, conj_out);
+    else
+        k_scatter_out<cd><<<g, 256, 0, st>>>(N, perm, phih, (cd *)Phi, conj_out);
 }
 
 // --------------------------------------------------------------- P2M, L2P
@@ -441,7 +459,7 @@ static __device__ inline void bessel_012(int kind, cd z, cd &J0, cd &J1, cd &J2)
 }
 
 __global__ void k_s2t_pre(const NearPair *near, const BoxDev *boxes, const double *xyz,
-                          MediumDev M, const CompDev *comps, double a, double kp, cd *coef,
+                          MediumDev M, const CompDev *comps, double a, int node_cap, cd *coef,
                           int *flag)
 {
     const int CH = 64;
@@ -455,7 +473,8 @@ __global__ void k_s2t_pre(const NearPair *near, const BoxDev *boxes, const doubl
     int64_t npp = nB * nC;
     if (threadIdx.x == 0) {
         pl = make_plan(a, np.rhomax, np.dzmin, 3, false);
-        if (plan_nodes(pl) > (1 << 20)) {
+        if (plan_nodes(pl) > node_cap) {
+            // bounded work: flag the pair (the build reports LMFMM_ERR_QUAD) and clamp
             atomicOr(flag, 2);
             pl.nmid = 16;
             pl.nray = 0;
@@ -463,7 +482,6 @@ __global__ void k_s2t_pre(const NearPair *near, const BoxDev *boxes, const doubl
     }
     __syncthreads();
     int Q = plan_nodes(pl);
-    (void)kp;
     cd *cf = coef + np.coef0 * 5;
     for (int64_t e = threadIdx.x; e < npp * 5; e += blockDim.x) cf[e] = mkd(0.0);
     cd k = M.k[c.l], kpz = M.k[c.lp];
@@ -513,11 +531,11 @@ __global__ void k_s2t_pre(const NearPair *near, const BoxDev *boxes, const doubl
 }
 
 void launch_s2t_pre(int64_t nnear, const NearPair *near, const BoxDev *boxes, const double *xyz,
-                    const MediumDev &M, const CompDev *comps, double a, double kp, cd *coef,
+                    const MediumDev &M, const CompDev *comps, double a, int node_cap, cd *coef,
                     int *dflag, cudaStream_t st)
 {
     if (nnear <= 0) return;
-    k_s2t_pre<<<(unsigned)nnear, 128, 0, st>>>(near, boxes, xyz, M, comps, a, kp, coef, dflag);
+    k_s2t_pre<<<(unsigned)nnear, 128, 0, st>>>(near, boxes, xyz, M, comps, a, node_cap, coef, dflag);
 }
 
 // Phi_h(i) += G^{*star}(r_j, r_i) q_j for the near pairs, in helical form with

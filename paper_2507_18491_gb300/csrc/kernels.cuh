@@ -69,9 +69,10 @@ void launch_tab_batch(const GeomDev *dG, int g0, int nb, int qmax, const MediumD
 // k_fmm.cu
 cudaError_t configure_fmm_kernels();
 cudaError_t configure_tab_kernels();
-void launch_gather_in(int64_t N, const int64_t *perm, const cd *J, cd *qh, bool conj_in,
+// J / Phi: caller's [N][3] complex128 (LMFMM_C128) or complex64 (LMFMM_C64)
+void launch_gather_in(int64_t N, const int64_t *perm, const void *J, int dtype, cd *qh, bool conj_in,
                       cudaStream_t st);
-void launch_scatter_out(int64_t N, const int64_t *perm, const cd *phih, cd *Phi, bool conj_out,
+void launch_scatter_out(int64_t N, const int64_t *perm, const cd *phih, void *Phi, int dtype, bool conj_out,
                         cudaStream_t st);
 template <typename T>
 void launch_p2m(int p, int64_t nleaf, const int64_t *leaves, const BoxDev *boxes,
@@ -125,8 +126,10 @@ void tile_matrix_tc2(int p, const cd *M, void *img);   // host: P x P row-major 
 template <typename T>
 void launch_scale_tables(int p, int64_t g0, int64_t ng, const GeomDev *geoms, const cd *tab64,
                          cx<T> *tab, cudaStream_t st);
+// five Sommerfeld integrals per point pair of every near pair; a pair whose
+// k_rho rule needs more than node_cap nodes sets bit 2 of *dflag (clamped rule)
 void launch_s2t_pre(int64_t nnear, const NearPair *near, const BoxDev *boxes, const double *xyz,
-                    const MediumDev &M, const CompDev *comps, double a, double kp, cd *coef,
+                    const MediumDev &M, const CompDev *comps, double a, int node_cap, cd *coef,
                     int *dflag, cudaStream_t st);
 // matvec near field: 8 combined coefficients per point pair ([j][8][i] per near pair)
 void launch_s2t_combine(int64_t nnear, const NearPair *near, const BoxDev *boxes, const double *xyz,

@@ -7,6 +7,7 @@
 // device array of fixed size instead of memory obtained from cudaMalloc.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <string>
 
 #include "kernels.cuh"
@@ -21,9 +22,12 @@ namespace {
 
 // Host-side stand-in for the pair list, so that building it allocates
 // nothing either; its capacity bounds the number of (component, leaf pair)
-// records a call may use.
+// records a call may use.  h_pairs, the address cache below and the device
+// scratch are process-wide: g_lock serialises whole calls (pair list, copy,
+// kernels, wait), on every device and context.
 constexpr int64_t kMaxPairs = 1 << 16;
 NearPair h_pairs[kMaxPairs];
+std::mutex g_lock;
 
 // Device address of g_noalloc_scratch, looked up once per device with that
 // device current (the symbol name in host code is only a stand-in).
@@ -74,6 +78,7 @@ extern "C" lmfmm_status lmfmm_direct_noalloc(lmfmm_ctx *ctx, const lmfmm_c128 *J
         ctx->err = std::string("direct_noalloc: cudaSetDevice: ") + cudaGetErrorString(e);
         return LMFMM_ERR_CUDA;
     }
+    std::lock_guard<std::mutex> hold(g_lock);
     void *scratch = nullptr;
     lmfmm_status s = scratch_address(ctx, &scratch);
     if (s) return s;
@@ -88,51 +93,12 @@ extern "C" lmfmm_status lmfmm_direct_noalloc(lmfmm_ctx *ctx, const lmfmm_c128 *J
         return LMFMM_ERR_STATE;
     }
     // every (component, source leaf, target leaf) pair, as in lmfmm_direct
-    int64_t np = 0, npp = 0;
-    const int D = ctx->depth;
-    for (int ci = 0; ci < (int)ctx->comps.size(); ++ci) {
-        const CompDev &c = ctx->comps[ci];
-        for (int64_t bs = ctx->lvl0[c.l][D]; bs < ctx->lvl1[c.l][D]; ++bs)
-            for (int64_t bt = ctx->lvl0[c.lp][D]; bt < ctx->lvl1[c.lp][D]; ++bt) {
-                if (np >= kMaxPairs) {
-                    ctx->err = "direct_noalloc: more than " + std::to_string(kMaxPairs) +
-                               " leaf pairs (use lmfmm_direct)";
-                    return LMFMM_ERR_ARG;
-                }
-                const Box &B = ctx->boxes[bs], &C = ctx->boxes[bt];
-                double smn = 1e300, smx = -1e300, tmn = 1e300, tmx = -1e300;
-                double bl[2] = {1e300, 1e300}, bh[2] = {-1e300, -1e300};
-                double cl[2] = {1e300, 1e300}, ch[2] = {-1e300, -1e300};
-                for (int64_t t = B.p0; t < B.p1; ++t) {
-                    double z = comp_src_z(c, ctx->sxyz[3 * t + 2]);
-                    smn = std::min(smn, z);
-                    smx = std::max(smx, z);
-                    for (int a = 0; a < 2; ++a) {
-                        bl[a] = std::min(bl[a], ctx->sxyz[3 * t + a]);
-                        bh[a] = std::max(bh[a], ctx->sxyz[3 * t + a]);
-                    }
-                }
-                for (int64_t t = C.p0; t < C.p1; ++t) {
-                    double z = comp_tgt_z(c, ctx->sxyz[3 * t + 2]);
-                    tmn = std::min(tmn, z);
-                    tmx = std::max(tmx, z);
-                    for (int a = 0; a < 2; ++a) {
-                        cl[a] = std::min(cl[a], ctx->sxyz[3 * t + a]);
-                        ch[a] = std::max(ch[a], ctx->sxyz[3 * t + a]);
-                    }
-                }
-                NearPair &q = h_pairs[np++];
-                q = NearPair{};
-                q.comp = ci;
-                q.src = bs;
-                q.tgt = bt;
-                q.coef0 = npp;
-                q.dzmin = c.s > 0 ? smn - tmx : tmn - smx;
-                double mx = std::max(std::fabs(bh[0] - cl[0]), std::fabs(ch[0] - bl[0]));
-                double my = std::max(std::fabs(bh[1] - cl[1]), std::fabs(ch[1] - bl[1]));
-                q.rhomax = std::sqrt(mx * mx + my * my);
-                npp += (B.p1 - B.p0) * (C.p1 - C.p0);
-            }
+    int64_t npp = 0;
+    const int64_t np = all_leaf_pairs(ctx, h_pairs, kMaxPairs, &npp);
+    if (np < 0) {
+        ctx->err = "direct_noalloc: more than " + std::to_string(kMaxPairs) +
+                   " leaf pairs (use lmfmm_direct)";
+        return LMFMM_ERR_ARG;
     }
     // layout in the scratch: pair records, then 5 complex coefficients per point pair
     size_t off_pairs = 0;
@@ -151,16 +117,15 @@ extern "C" lmfmm_status lmfmm_direct_noalloc(lmfmm_ctx *ctx, const lmfmm_c128 *J
         ctx->err = std::string("direct_noalloc: copy of the pair list: ") + cudaGetErrorString(e);
         return LMFMM_ERR_CUDA;
     }
-    double km = 0;
-    for (int j = 0; j <= ctx->med.L; ++j) km = std::max(km, std::hypot(ctx->med.k[j].x, ctx->med.k[j].y));
-    const double a = 1.5 * km + 0.75;
+    const double a = medium_a(ctx->med);
     // the coefficient range is zero-filled by the precomputation kernel itself,
-    // the helical result buffer here
-    launch_gather_in(ctx->N, perm, (const cd *)J, qh, false, st);
+    // the helical result buffer and the quadrature flag here
+    cudaMemsetAsync(flag, 0, sizeof(int), st);
+    launch_gather_in(ctx->N, perm, J, LMFMM_C128, qh, false, st);
     cudaMemsetAsync(ph, 0, (size_t)ctx->N * 3 * sizeof(cd), st);
-    launch_s2t_pre(np, dpairs, boxes, xyz, ctx->med, comps, a, 0.5 * a, coef, flag, st);
+    launch_s2t_pre(np, dpairs, boxes, xyz, ctx->med, comps, a, ctx->prm.quad_node_cap, coef, flag, st);
     launch_s2t_apply(np, dpairs, boxes, xyz, coef, qh, ph, st);
-    launch_scatter_out(ctx->N, perm, ph, (cd *)Phi, false, st);
+    launch_scatter_out(ctx->N, perm, ph, Phi, LMFMM_C128, false, st);
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) {
         ctx->err = std::string("direct_noalloc: ") + cudaGetErrorString(e);
         return LMFMM_ERR_CUDA;

@@ -16,11 +16,13 @@ from . import build as _build
 
 _lib = None
 
-OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_STATE, ERR_QUAD, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_STATE, ERR_QUAD, ERR_UNSUPPORTED, ERR_TIMEOUT = (
+    0, -1, -2, -3, -4, -5, -6, -7)
 FP64, MIXED = 0, 1
+C128, C64 = 0, 1
 
 
-class C128(ctypes.Structure):
+class _Complex128(ctypes.Structure):
     _fields_ = [("re", ctypes.c_double), ("im", ctypes.c_double)]
 
 
@@ -28,7 +30,7 @@ class Params(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int), ("depth", ctypes.c_int), ("leaf_cap", ctypes.c_int),
                 ("theta", ctypes.c_double), ("eta", ctypes.c_double),
                 ("quad_tol", ctypes.c_double), ("precision", ctypes.c_int),
-                ("tensor_cores", ctypes.c_int)]
+                ("tensor_cores", ctypes.c_int), ("quad_node_cap", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -39,12 +41,15 @@ class Stats(ctypes.Structure):
                 ("n_near_point_pairs", ctypes.c_int64), ("n_quad_nodes", ctypes.c_int64),
                 ("bytes_tables", ctypes.c_double), ("ms_setup", ctypes.c_double),
                 ("ms_stage", ctypes.c_double * 8), ("m2l_columns", ctypes.c_int64),
-                ("m2l_kernel", ctypes.c_int)]
+                ("m2l_kernel", ctypes.c_int), ("launches", ctypes.c_int),
+                ("n_geometries_same_layer", ctypes.c_int64), ("ms_tabulate", ctypes.c_double),
+                ("tab_flops", ctypes.c_double)]
 
 
 EXPORTS = ["lmfmm_default_params", "lmfmm_create", "lmfmm_set_layers", "lmfmm_set_points",
-           "lmfmm_build", "lmfmm_matvec", "lmfmm_matvec_host", "lmfmm_matvec_adjoint",
-           "lmfmm_direct", "lmfmm_direct_noalloc", "lmfmm_densities", "lmfmm_m2l_table", "lmfmm_translation_matrix",
+           "lmfmm_set_points_device", "lmfmm_build", "lmfmm_matvec", "lmfmm_matvec_host",
+           "lmfmm_matvec_adjoint", "lmfmm_check", "lmfmm_test_set_status", "lmfmm_direct",
+           "lmfmm_direct_noalloc", "lmfmm_densities", "lmfmm_m2l_table", "lmfmm_translation_matrix",
            "lmfmm_get_stats", "lmfmm_last_error", "lmfmm_destroy"]
 
 
@@ -72,17 +77,20 @@ def load():
     sig = {
         "lmfmm_default_params": [ctypes.POINTER(Params)],
         "lmfmm_create": [ctypes.POINTER(P), ctypes.POINTER(Params), i],
-        "lmfmm_set_layers": [P, i, ctypes.POINTER(d), ctypes.POINTER(C128)],
+        "lmfmm_set_layers": [P, i, ctypes.POINTER(d), ctypes.POINTER(_Complex128)],
         "lmfmm_set_points": [P, i64, ctypes.POINTER(d)],
+        "lmfmm_set_points_device": [P, i64, P, P],
         "lmfmm_build": [P, P],
-        "lmfmm_matvec": [P, P, P, P],
-        "lmfmm_matvec_host": [P, P, P, P],
-        "lmfmm_matvec_adjoint": [P, P, P, P],
+        "lmfmm_matvec": [P, P, i, P, P],
+        "lmfmm_matvec_host": [P, P, i, P, P],
+        "lmfmm_matvec_adjoint": [P, P, i, P, P],
+        "lmfmm_check": [P, P],
+        "lmfmm_test_set_status": [P, i],
         "lmfmm_direct": [P, P, P, P],
         "lmfmm_direct_noalloc": [P, P, P, P],
         "lmfmm_densities": [P, i, i, i64, P, P, P],
         "lmfmm_m2l_table": [P, i, i, i, i, d, d, d, P, P],
-        "lmfmm_translation_matrix": [i, C128, ctypes.POINTER(d), P, P],
+        "lmfmm_translation_matrix": [i, _Complex128, ctypes.POINTER(d), P, P],
         "lmfmm_get_stats": [P, ctypes.POINTER(Stats)],
         "lmfmm_last_error": [P],
         "lmfmm_destroy": [P],
@@ -121,6 +129,18 @@ def _dptr(t, n3=None):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _field(t, like=None):
+    """(pointer, dtype code) of a contiguous complex128/complex64 CUDA tensor [N, 3]."""
+    import torch
+    codes = {torch.complex128: C128, torch.complex64: C64}
+    if not (t.is_cuda and t.dtype in codes and t.is_contiguous() and t.dim() == 2
+            and t.shape[1] == 3):
+        raise ValueError("expected a contiguous complex128 or complex64 CUDA tensor [N, 3]")
+    if like is not None and (t.dtype != like.dtype or t.shape != like.shape):
+        raise ValueError("input and output must have the same dtype and shape")
+    return ctypes.c_void_p(t.data_ptr()), codes[t.dtype]
+
+
 # ------------------------------------------------------------ C-ABI mirror
 def default_params() -> Params:
     prm = Params()
@@ -137,7 +157,7 @@ def create(prm: Params, device: int = 0):
 def set_layers(ctx, d, k):
     d = np.ascontiguousarray(np.asarray(d, np.float64).reshape(-1))
     k = np.asarray(k, np.complex128).reshape(-1)
-    karr = (C128 * k.size)(*[C128(float(v.real), float(v.imag)) for v in k])
+    karr = (_Complex128 * k.size)(*[_Complex128(float(v.real), float(v.imag)) for v in k])
     _check(load().lmfmm_set_layers(ctx, int(d.size), d.ctypes.data_as(ctypes.POINTER(
         ctypes.c_double)), karr), ctx)
 
@@ -148,23 +168,50 @@ def set_points(ctx, xyz):
                                    xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), ctx)
 
 
+def set_points_device(ctx, xyz, stream=None):
+    """Points from a contiguous float64 CUDA tensor [N, 3]."""
+    import torch
+    if not (xyz.is_cuda and xyz.dtype == torch.float64 and xyz.is_contiguous() and xyz.dim() == 2
+            and xyz.shape[1] == 3):
+        raise ValueError("expected a contiguous float64 CUDA tensor [N, 3]")
+    _check(load().lmfmm_set_points_device(ctx, int(xyz.shape[0]), ctypes.c_void_p(xyz.data_ptr()),
+                                          _stream(stream)), ctx)
+
+
 def build(ctx, stream=None):
     _check(load().lmfmm_build(ctx, _stream(stream)), ctx)
 
 
 def matvec(ctx, J, Phi, stream=None):
-    _check(load().lmfmm_matvec(ctx, _dptr(J), _dptr(Phi), _stream(stream)), ctx)
+    """Phi = A J on the device (complex128 or complex64 tensors [N, 3], same dtype)."""
+    pj, code = _field(J)
+    pp, _ = _field(Phi, like=J)
+    _check(load().lmfmm_matvec(ctx, pj, code, pp, _stream(stream)), ctx)
 
 
 def matvec_adjoint(ctx, y, Phi, stream=None):
-    _check(load().lmfmm_matvec_adjoint(ctx, _dptr(y), _dptr(Phi), _stream(stream)), ctx)
+    py, code = _field(y)
+    pp, _ = _field(Phi, like=y)
+    _check(load().lmfmm_matvec_adjoint(ctx, py, code, pp, _stream(stream)), ctx)
+
+
+def check(ctx, stream=None):
+    """Wait for the stream and raise if a device wait of the matvecs gave up."""
+    _check(load().lmfmm_check(ctx, _stream(stream)), ctx)
+
+
+def test_set_status(ctx, bits):
+    _check(load().lmfmm_test_set_status(ctx, int(bits)), ctx)
 
 
 def matvec_host(ctx, J: np.ndarray, Phi: np.ndarray, stream=None):
+    codes = {np.dtype(np.complex128): C128, np.dtype(np.complex64): C64}
     for a in (J, Phi):
-        if a.dtype != np.complex128 or not a.flags.c_contiguous:
-            raise ValueError("expected contiguous complex128 arrays")
-    _check(load().lmfmm_matvec_host(ctx, ctypes.c_void_p(J.ctypes.data),
+        if a.dtype not in codes or not a.flags.c_contiguous:
+            raise ValueError("expected contiguous complex128 or complex64 arrays")
+    if J.dtype != Phi.dtype or J.shape != Phi.shape:
+        raise ValueError("J and Phi must have the same dtype and shape")
+    _check(load().lmfmm_matvec_host(ctx, ctypes.c_void_p(J.ctypes.data), codes[J.dtype],
                                     ctypes.c_void_p(Phi.ctypes.data), _stream(stream)), ctx)
 
 
@@ -194,7 +241,7 @@ def translation_matrix(p, k, t):
     up = np.zeros((P, P), np.complex128)
     dn = np.zeros((P, P), np.complex128)
     t = np.ascontiguousarray(np.asarray(t, np.float64))
-    _check(load().lmfmm_translation_matrix(int(p), C128(float(np.real(k)), float(np.imag(k))),
+    _check(load().lmfmm_translation_matrix(int(p), _Complex128(float(np.real(k)), float(np.imag(k))),
                                            t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                            ctypes.c_void_p(up.ctypes.data),
                                            ctypes.c_void_p(dn.ctypes.data)))
@@ -225,11 +272,14 @@ class Operator:
     """The reaction-field operator of one point set in one layered medium.
 
     ``Operator(d, k, xyz, p=...)`` sets up the context; ``build()`` runs the
-    setup on the GPU; ``matvec(J)`` returns A J (torch complex128, [N,3])."""
+    setup on the GPU; ``matvec(J)`` returns A J (torch complex128 or complex64,
+    [N,3], the dtype of J); ``check()`` raises if a device wait gave up."""
 
     def __init__(self, d, k, xyz, p=8, depth=-1, leaf_cap=64, theta=0.55, eta=0.1,
-                 precision=FP64, tensor_cores=True, device=0):
+                 precision=FP64, tensor_cores=True, device=0, quad_node_cap=None):
         prm = default_params()
+        if quad_node_cap is not None:
+            prm.quad_node_cap = int(quad_node_cap)
         prm.p, prm.depth, prm.leaf_cap = int(p), int(depth), int(leaf_cap)
         prm.theta, prm.eta, prm.precision = float(theta), float(eta), int(precision)
         prm.tensor_cores = int(tensor_cores)
@@ -256,6 +306,9 @@ class Operator:
             out = torch.empty_like(y)
         matvec_adjoint(self.ctx, y, out, stream)
         return out
+
+    def check(self, stream=None):
+        check(self.ctx, stream)
 
     def direct(self, J, out=None, stream=None):
         import torch

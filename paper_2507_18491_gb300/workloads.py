@@ -151,3 +151,35 @@ def points_in_layers(rng, d, counts, margin=0.1, xy=1.0, height=1.0):
 
 def currents(rng, n):
     return _currents(rng, n, False)
+
+
+def accuracy_sample(w, n_targets, n_random_sources, n_neighbours, band, seed=11,
+                    near_fraction=0.5):
+    """Seeded target and source subsets for checking a matvec against a direct
+    sum (Err_2 / Err_max of Section 4 over the targets).
+
+    Half of the targets (``near_fraction``) are drawn among the points closer
+    than ``band`` to an interface, where the images of nearby sources fall next
+    to the targets and the near-field (direct) sums of the FMM are exercised;
+    the rest uniformly.  The sources are ``n_random_sources`` uniform draws plus
+    the ``n_neighbours`` nearest points of every target (itself included, so
+    the self term is in the sum).  Returns sorted unique index arrays
+    (targets, sources)."""
+    rng = np.random.default_rng(seed)
+    z = w.xyz[:, 2]
+    dist = np.min(np.abs(z[:, None] - np.asarray(w.d, float)[None, :]), axis=1) \
+        if np.asarray(w.d).size else np.full(w.N, np.inf)
+    close = np.flatnonzero(dist < band)
+    n_near = min(int(round(near_fraction * n_targets)), close.size)
+    tg_near = rng.choice(close, n_near, replace=False) if n_near else np.zeros(0, np.int64)
+    rest = np.setdiff1d(np.arange(w.N), tg_near)
+    tg_far = rng.choice(rest, n_targets - n_near, replace=False)
+    targets = np.unique(np.concatenate([tg_near, tg_far])).astype(np.int64)
+    src = [rng.choice(w.N, min(n_random_sources, w.N), replace=False)]
+    for t in targets:
+        d2 = np.sum((w.xyz - w.xyz[t]) ** 2, axis=1)
+        src.append(np.argpartition(d2, n_neighbours)[:n_neighbours] if n_neighbours < w.N
+                   else np.arange(w.N))
+        src.append(np.array([t]))
+    sources = np.unique(np.concatenate(src)).astype(np.int64)
+    return targets, sources

@@ -53,3 +53,19 @@ def test_bad_params_rejected_before_device_use(lib):
         prm.tensor_cores = bad
         assert lib.lmfmm_create(ctypes.byref(h), ctypes.byref(prm), 0) == lmfmm.ERR_ARG
         assert b"tensor_cores" in lib.lmfmm_last_error(None)
+
+
+def test_quad_node_cap_default_and_range(lib):
+    prm = lmfmm.default_params()
+    assert prm.quad_node_cap == 1 << 20 and prm.tensor_cores == 1
+    prm.quad_node_cap = 10
+    h = ctypes.c_void_p()
+    assert lib.lmfmm_create(ctypes.byref(h), ctypes.byref(prm), 0) == lmfmm.ERR_ARG
+    assert b"quad_node_cap" in lib.lmfmm_last_error(None)
+
+
+def test_null_context_is_an_argument_error(lib):
+    assert lib.lmfmm_check(None, None) == lmfmm.ERR_ARG
+    assert lib.lmfmm_test_set_status(None, 4) == lmfmm.ERR_ARG
+    assert lib.lmfmm_matvec(None, None, lmfmm.C128, None, None) == lmfmm.ERR_ARG
+    assert lib.lmfmm_set_points_device(None, 1, None, None) == lmfmm.ERR_ARG

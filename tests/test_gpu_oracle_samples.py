@@ -1,0 +1,123 @@
+"""GPU matvecs and tables against stored oracle values (tests/golden/oracle_*.npz,
+written by tests/golden/make_oracle_samples.py from the CPU oracle alone; a
+reader whose regenerated inputs differ recomputes them with the oracle).
+
+Error measures of Section 4 over the sampled targets: Err_2 (relative L2) and
+Err_max (largest pointwise relative error).  Bars: the FP64 form 1e-6 (Err_2),
+the mixed form 1e-5; Err_max ten times the Err_2 bar."""
+import numpy as np
+import pytest
+
+import oracle_refs as R
+from paper_2507_18491_gb300 import lmfmm
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def run(w, J, precision, p, depth, theta, tensor_cores=1):
+    op = lmfmm.Operator(w.d, w.k, w.xyz, p=p, depth=depth, theta=theta, precision=precision,
+                        tensor_cores=tensor_cores).build()
+    try:
+        got = op.matvec(torch.from_numpy(J).cuda()).cpu().numpy()
+        op.check()
+        st = op.stats()
+    finally:
+        op.close()
+    return got, st
+
+
+@pytest.fixture(scope="module")
+def two_layer():
+    return R.reference("two_layer_n512")
+
+
+@pytest.mark.parametrize("precision,p,theta,bar", [
+    (lmfmm.FP64, 6, 0.55, 1e-3),     # the workload's nominal p: truncation ~3e-4
+    (lmfmm.FP64, 10, 0.4, 1e-6),
+    (lmfmm.MIXED, 10, 0.4, 1e-5),
+])
+def test_two_layer_n512_every_target(two_layer, precision, p, theta, bar):
+    w, tg, src, J, ref = two_layer
+    assert tg.size == w.N == 512
+    got, _ = run(w, J, precision, p, w.depth, theta, tensor_cores=3)
+    e2, em = R.err2(got[tg], ref), R.errmax(got[tg], ref)
+    print("two-layer N=512 p=%d prec=%d: Err_2 %.3e Err_max %.3e" % (p, precision, e2, em))
+    assert e2 < bar and em < 10 * bar
+
+
+@pytest.fixture(scope="module")
+def three_layer_full():
+    return R.reference("three_layer_n65536")
+
+
+@pytest.mark.parametrize("precision,tensor_cores,bar", [(lmfmm.FP64, 1, 1e-6), (lmfmm.MIXED, 3, 1e-5)])
+def test_three_layer_full_size(three_layer_full, precision, tensor_cores, bar):
+    """Three layers, N = 65536, p = 10, depth 5 at full size; 256 targets (half
+    of them next to an interface) against ~1500 sources that include each
+    target's nearest neighbours, so that near-field pairs are in the sum."""
+    w, tg, src, J, ref = three_layer_full
+    got, st = run(w, J, precision, 10, 5, 0.5, tensor_cores)
+    e2, em = R.err2(got[tg], ref), R.errmax(got[tg], ref)
+    print("three-layer N=65536 p=10: Err_2 %.3e Err_max %.3e (%d targets, %d sources, %d near point pairs)"
+          % (e2, em, tg.size, src.size, st["n_near_point_pairs"]))
+    assert e2 < bar and em < 10 * bar
+
+
+@pytest.fixture(scope="module")
+def three_layer_small():
+    return R.reference("three_layer_n4096")
+
+
+@pytest.mark.parametrize("p", [4, 7, 8, 12, 13, 15])
+def test_tensor_core_forms_against_the_oracle(three_layer_small, p):
+    """Every M2L product form against the oracle at p = 4 ... 15: the tensor-core
+    forms (persistent bf16 kernel p <= 12, streamed TF32 kernel) add at most a
+    few 1e-7 to the FP64 form's truncation error."""
+    w, tg, src, J, ref = three_layer_small
+    e = {}
+    got, _ = run(w, J, lmfmm.FP64, p, 3, 0.5)
+    e["fp64"] = R.err2(got[tg], ref)
+    for tc, kern in ((0, 1), (1, 3 if p <= 12 else 2), (2, 2), (3, 3 if p <= 12 else 2)):
+        got, st = run(w, J, lmfmm.MIXED, p, 3, 0.5, tc)
+        assert st["m2l_kernel"] == kern
+        e[tc] = R.err2(got[tg], ref)
+    print("p=%d vs oracle: fp64 %.3e  simt %.3e  tc1 %.3e  tc2 %.3e  tc3 %.3e"
+          % (p, e["fp64"], e[0], e[1], e[2], e[3]))
+    for tc in (0, 1, 2, 3):
+        assert e[tc] < e["fp64"] + 2e-6, tc
+
+
+def test_m2l_tables_p12_match_oracle():
+    """The p = 12 tables of the four-layer medium (the benchmark's), entry by
+    entry against the oracle's definitional integrals, per (n', nu) block of the
+    stored degrees (0-3, 6, 9, 11, 12)."""
+    z = R.tables("tables_p12")
+    p = int(z["p"])
+    P = (p + 1) ** 2
+    prm = lmfmm.default_params()
+    prm.p = p
+    ctx = lmfmm.create(prm, 0)
+    try:
+        lmfmm.set_layers(ctx, z["d"], z["k"])
+        for gi, (l, lp, tu, su, rho, zs, zt) in enumerate(z["geoms"]):
+            out = torch.empty((5, P, P), dtype=torch.complex128, device="cuda")
+            lmfmm.m2l_table(ctx, int(l), int(lp), int(tu), int(su), rho, zs, zt, out)
+            ix = z["index"]
+            got = out.cpu().numpy()[:, ix][:, :, ix]
+            deg = np.floor(np.sqrt(ix + 0.5)).astype(int)
+            worst = 0.0
+            for t in range(5):
+                ref = z["tables"][gi, t]
+                for n1 in z["degrees"]:
+                    for nu in z["degrees"]:
+                        rs, cs = deg == nu, deg == n1
+                        r = ref[np.ix_(rs, cs)]
+                        sc = np.max(np.abs(r))
+                        if sc == 0:
+                            continue
+                        worst = max(worst, np.max(np.abs(got[t][np.ix_(rs, cs)] - r)) / sc)
+            print("geometry %d: worst blockwise relative difference %.3e" % (gi, worst))
+            assert worst < 1e-9
+    finally:
+        lmfmm.destroy(ctx)

@@ -43,3 +43,27 @@ def test_noalloc_rejects_work_beyond_its_scratch():
         lmfmm.direct_noalloc(op.ctx, J, out)
     assert ei.value.code == lmfmm.ERR_ARG and "scratch" in str(ei.value)
     op.close()
+
+
+def test_noalloc_across_contexts_of_different_sizes():
+    """The shared array keeps whatever the previous call left: a larger context
+    (more leaf pairs and coefficients), then a smaller one with another N and
+    depth, then the larger one again must each reproduce lmfmm_direct."""
+    rng = np.random.default_rng(41)
+    d = np.array([0.0, -1.2])
+    k = np.array([0.8, 1.5, 2.0]) + 0.01j
+    big = W.points_in_layers(rng, d, [60, 60, 60], margin=0.1, xy=0.8)
+    small = W.points_in_layers(rng, d, [25, 0, 30], margin=0.1, xy=0.8)
+    ops = {"big": lmfmm.Operator(d, k, big, p=4, depth=1).build(),
+           "small": lmfmm.Operator(d, k, small, p=4, depth=2).build()}
+    try:
+        for name in ("big", "small", "big"):
+            op = ops[name]
+            J = torch.from_numpy(W.currents(rng, op.N)).cuda()
+            ref = op.direct(J).cpu().numpy()
+            out = torch.empty_like(J)
+            lmfmm.direct_noalloc(op.ctx, J, out)
+            assert _rel(out.cpu().numpy(), ref) < 1e-12, name
+    finally:
+        for op in ops.values():
+            op.close()
