@@ -10,7 +10,8 @@ sampled targets in the same run.  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--precision fp64|mixed] [--tensor-cores 0|1|2|3]
-                  [--workload four_layer|three_layer|two_layer|four_layer_small|three_layer_small]
+                  [--workload four_layer|three_layer|two_layer|four_layer_small|three_layer_small
+                              |paper_2layer|paper_3layer]
 
 Multi-GPU: every rank runs an independent replica of the workload (the
 reaction components are independent FMMs, no data exchange is needed);
@@ -66,6 +67,11 @@ def workload(name, seed_shift=0):
         return W.three_layer(n=8192, seed=1002 + seed_shift, p=8), dict(depth=4, theta=0.55)
     if name == "two_layer":
         return W.two_layer_small(seed=1001 + seed_shift), dict(depth=2, theta=0.4)
+    if name in ("paper_2layer", "paper_3layer"):
+        # Section 4 efficiency test: 10^6 uniform points per layer in unit cubes, p = 8
+        layers = 2 if name == "paper_2layer" else 3
+        return W.paper_table_uniform(m=10 ** 6, layers=layers, seed=1006 + seed_shift, p=8), \
+            dict(depth=5, theta=0.55)
     raise SystemExit("unknown workload " + name)
 
 
@@ -162,7 +168,14 @@ def cpu_baseline(w, sample_sources=1500, sample_targets=8, threads=0):
 
 
 SAMPLE_OF = {"four_layer_clusters_n1048576": "four_layer_n1048576", "three_layer_n65536": "three_layer_n65536",
-             "two_layer_n512": "two_layer_n512"}
+             "two_layer_n512": "two_layer_n512", "paper_table_2layer_m1000000": "paper_2layer_m1000000",
+             "paper_table_3layer_m1000000": "paper_3layer_m1000000"}
+
+# The paper's own timings of the reaction part on this workload (Table Cputime_N_p8,
+# M = 10^6 per layer, p = 8, one Xeon E5-2699 v4 core, setup and all passes included):
+# sum of the Phi^r rows -> 2 x 10^6 targets in 94.39 s, 3 x 10^6 in 417.90 s.
+PAPER_MTARGETS = {"paper_table_2layer_m1000000": 2e6 / 94.39 / 1e6,
+                  "paper_table_3layer_m1000000": 3e6 / 417.90 / 1e6}
 
 
 def _samples():
@@ -331,7 +344,8 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "Mtargets/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": (value / PAPER_MTARGETS[w.name]) if w.name in PAPER_MTARGETS else None,
         "dtype": "f64" if prec == lmfmm.FP64 else "f32", "data": "synthetic",
         "config": {"workload": w.name, "N": w.N, "layers": int(w.d.size + 1), "p": p,
                    "depth": st["depth"], "theta": opt["theta"], "precision": args.precision,

@@ -277,14 +277,27 @@ lmfmm_status build_host_structures(lmfmm_ctx *ctx)
             }
         }
     }
-    // geometry deduplication: (comp, level, dx^2+dy^2 in cells, iz_s, iz_t)
+    // geometry deduplication.  A table depends on the horizontal distance rho and
+    // on the mapped heights through Z = e^{i s (k_z z_s - k'_z z_t)} (Section 3.4,
+    // eq. onedimensionintegral): key (comp, level, dx^2 + dy^2 in cells, iz_s, iz_t).
+    // Within a layer (l = l', k = k') Z depends on z_s - z_t alone, so every pair
+    // of equal vertical offset shares one table: key (comp, level, rho^2, offset),
+    // the offset in half cells of the mapped centres (a mirrored box's mapped
+    // height runs against its cell index).
     std::map<std::tuple<int, int, int64_t, int, int>, int> gid;
     std::vector<int> pg(far.size());
     ctx->geoms.clear();
     for (size_t i = 0; i < far.size(); ++i) {
         const Box &B = ctx->boxes[far[i].src], &C = ctx->boxes[far[i].tgt];
         int64_t ddx = B.ix - C.ix, ddy = B.iy - C.iy;
-        auto key = std::make_tuple(far[i].comp, far[i].level, ddx * ddx + ddy * ddy, B.iz, C.iz);
+        const CompDev &cc = ctx->comps[far[i].comp];
+        int kz0 = B.iz, kz1 = C.iz;
+        if (cc.l == cc.lp) {
+            const int ss = cc.has_src_refl ? -1 : 1, st = cc.has_tgt_refl ? -1 : 1;
+            kz0 = ss * (2 * B.iz + 1) - st * (2 * C.iz + 1);
+            kz1 = 0;
+        }
+        auto key = std::make_tuple(far[i].comp, far[i].level, ddx * ddx + ddy * ddy, kz0, kz1);
         auto it = gid.find(key);
         if (it == gid.end()) {
             Geom g{};

@@ -17,7 +17,9 @@ Cases
     four_layer_n1048576    128 targets, ~1400 sources (random + nearest neighbours)
     three_layer_n4096      64 targets, ~550 sources (tensor-core sweep in p)
     paper_2layer_m1000 /
-    paper_3layer_m1000     64 targets, ~700 sources (the Section 4 media)
+    paper_3layer_m1000     64 targets, ~700 sources (the Section 4 media, 1000 per layer)
+    paper_2layer_m1000000 /
+    paper_3layer_m1000000  64 targets, ~700 sources (the same, 10^6 points per layer)
   M2L tables (eq. onedimensionintegral) at p = 12, four-layer medium:
     tables_p12             two geometries, every (sigma, kappa), the (n', nu) blocks of
                            degrees 0-3, 6, 9, 11, 12
@@ -45,6 +47,8 @@ DIRECT = {
     "three_layer_n4096": (lambda: W.three_layer(n=4096, p=8, depth=3), (64, 300, 4, 0.15)),
     "paper_2layer_m1000": (lambda: W.paper_table_uniform(m=1000, layers=2), (64, 400, 6, 0.2)),
     "paper_3layer_m1000": (lambda: W.paper_table_uniform(m=1000, layers=3), (64, 400, 6, 0.2)),
+    "paper_2layer_m1000000": (lambda: W.paper_table_uniform(m=10 ** 6, layers=2), (64, 400, 6, 0.05)),
+    "paper_3layer_m1000000": (lambda: W.paper_table_uniform(m=10 ** 6, layers=3), (64, 400, 6, 0.05)),
 }
 
 # four-layer medium of the benchmark; (l, lp, target up, source up, rho, zs, zt) of

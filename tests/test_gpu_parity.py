@@ -275,3 +275,31 @@ def test_stats_before_first_matvec():
     torch.cuda.synchronize()
     assert op.stats()["ms_stage"]["total"] > 0
     op.close()
+
+
+def test_same_layer_tables_shared_by_equal_offsets():
+    """The build keys same-layer tables on (level, rho, z_s - z_t): the device
+    tabulation of two geometries with equal offsets gives the same table."""
+    P = (8 + 1) ** 2
+    ctx = _ctx(D4, K4, p=8)
+    try:
+        out = []
+        for zs, zt in ((-0.2, -0.9), (-0.35, -1.05)):     # layer 1, images across z = 0
+            t = torch.empty((5, P, P), dtype=torch.complex128, device="cuda")
+            lmfmm.m2l_table(ctx, 1, 1, 1, 0, 0.35, zs + 0.6, zt, t)
+            out.append(t.cpu().numpy())
+    finally:
+        lmfmm.destroy(ctx)
+    for t in range(5):
+        sc = np.max(np.abs(out[0][t]))
+        assert np.max(np.abs(out[0][t] - out[1][t])) < 1e-13 * sc, t
+
+
+def test_geometry_count_after_offset_merge():
+    """Same-layer geometries of the four-layer clustered workload (N = 2^17,
+    depth 4) are counted once per (level, rho, offset)."""
+    w = W.four_layer_clusters(n=1 << 17)
+    op = lmfmm.Operator(w.d, w.k, w.xyz, p=4, depth=4, theta=0.55).build()
+    st = op.stats()
+    op.close()
+    assert 0 < st["n_geometries_same_layer"] < st["n_geometries"]

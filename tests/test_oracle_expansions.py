@@ -117,3 +117,20 @@ def test_me_m2l_le_chain_converges(comp):
         got = _chain(D3, K3, l, lp, tu, su, rj, ri, q, cs_off, ct_off, p)
         errs.append(np.linalg.norm(got - ref) / np.linalg.norm(ref))
     assert errs[1] < 1e-6 and errs[1] < 0.05 * errs[0], errs
+
+
+def test_same_layer_tables_depend_on_the_vertical_offset_only():
+    """Eq. onedimensionintegral: within one layer (k = k') the vertical factor
+    e^{i s (k_z z_s - k'_z z_t)} depends on z_s - z_t alone, so two M2L
+    geometries of equal (rho, z_s - z_t) share a table; between layers they do
+    not.  This is what lets the build key same-layer tables on the offset."""
+    d, k = np.array([0.0, -1.2]), np.array([0.8, 1.5, 2.0]) + 0.01j
+    p, rho = 3, 0.4
+    # layer 1, target up / source down (s = +1): mapped source above the target
+    a = O.m2l_table(d, k, 1, 1, 1, 0, 1, 0, p, rho, 0.30, -0.50, rtol=1e-13)
+    b = O.m2l_table(d, k, 1, 1, 1, 0, 1, 0, p, rho, 0.45, -0.35, rtol=1e-13)
+    assert np.max(np.abs(a - b)) < 1e-11 * np.max(np.abs(a))
+    # layers 0 and 1 (k != k'): shifting both heights changes the table
+    c = O.m2l_table(d, k, 0, 1, 1, 1, 1, 0, p, rho, 0.45, -0.5, rtol=1e-13)
+    e = O.m2l_table(d, k, 0, 1, 1, 1, 1, 0, p, rho, 0.60, -0.35, rtol=1e-13)
+    assert np.max(np.abs(c - e)) > 1e-3 * np.max(np.abs(c))
