@@ -61,6 +61,11 @@ enum { LMFMM_FP64 = 0, LMFMM_MIXED = 1 };
 /* element type of caller buffers of currents and fields */
 enum { LMFMM_C128 = 0, LMFMM_C64 = 1 };
 
+/* parts of the dyadic Green's function a matvec applies (eq. layeredmediafields):
+ * the interface-induced reaction field, the free-space part Phi^f of sources in
+ * the target's own layer (self term excluded), or both */
+enum { LMFMM_REACTION = 0, LMFMM_FREE = 1, LMFMM_TOTAL = 2 };
+
 typedef struct {
     int p;             /* truncation order of the expansions, 1..16 (P = (p+1)^2 coefficients) */
     int depth;         /* octree leaf level (root = 0); < 0 selects it from leaf_cap */
@@ -82,6 +87,11 @@ typedef struct {
                           or a near box pair); beyond it lmfmm_build returns LMFMM_ERR_QUAD
                           (table: checked on the host before any launch; near pair: the
                           device loop is clamped and flags it).  Default 2^20. */
+    int components;    /* LMFMM_REACTION (default), LMFMM_FREE or LMFMM_TOTAL.  The free-space
+                          part (Section 2) is an FMM of its own over each layer's tree: the
+                          same P2M / M2M / L2L / L2P, M2L tables from the addition theorem
+                          with the Hessian folded in (host-built, run by the same M2L
+                          kernels) and a direct near field in FP64 */
 } lmfmm_params;
 
 typedef struct {
@@ -111,10 +121,16 @@ typedef struct {
                               Chebyshev integrals (80 (tau, tau', table) combinations x (p+2)
                               degrees x (2p+3) Bessel orders per node) and of the assembly
                               (5 P^2 (p+2) per geometry) */
+    int adjoint_transposed; /* 1: lmfmm_matvec_adjoint applies the transposed operators (FP64
+                               form, mixed form with tensor_cores = 0); 0: the reciprocity
+                               identity with the forward kernels (tensor-core forms) */
+    int64_t n_free_geometries;        /* free-space M2L tables (of n_geometries) */
+    int64_t n_free_near_point_pairs;  /* free-space near-field point pairs */
 } lmfmm_stats;
 
 /* Fill *prm with defaults (p = 8, depth from leaf_cap = 64, theta = 0.55,
- * eta = 0.1, quad_tol = 1e-15, FP64, tensor_cores = 1, quad_node_cap = 2^20). */
+ * eta = 0.1, quad_tol = 1e-15, FP64, tensor_cores = 1, quad_node_cap = 2^20,
+ * components = LMFMM_REACTION). */
 lmfmm_status lmfmm_default_params(lmfmm_params *prm);
 
 /* Create a context on CUDA device `device`.  *out receives the handle. */
@@ -155,12 +171,43 @@ lmfmm_status lmfmm_matvec(lmfmm_ctx *ctx, const void *J, int dtype, void *Phi, v
  * device status checked (lmfmm_check).  Pinned host memory is faster. */
 lmfmm_status lmfmm_matvec_host(lmfmm_ctx *ctx, const void *J, int dtype, void *Phi, void *stream);
 
-/* Phi = A^H y (device buffers of element type dtype).  The reaction operator
- * is complex symmetric (reciprocity, G(r,r') = G(r',r)^T, which the paper
- * invokes for summing over the first slot), so A^H y = conj(A conj(y)); this
- * applies exactly that.  Asynchronous like lmfmm_matvec. */
+/* out = A^T y, A the FMM operator as built (device buffers of element type
+ * dtype): every stage of the matvec replaced by its exact transpose, in
+ * reverse order -- the transposed helical maps, L2P^T (point values summed
+ * against the L2P functions into the leaf local expansions), L2L^T and M2M^T
+ * (transposed translation matrices, up and down the tree), M2L^T (transposed
+ * tables with the same per-pair factors), P2M^T (multipole expansions
+ * evaluated with the P2M functions) and the transposed near field.  So
+ * <x, A^T y> = <A x, y> holds to rounding, whatever the truncation.  FP64 form
+ * and mixed form with tensor_cores = 0 (LMFMM_ERR_UNSUPPORTED otherwise: the
+ * tensor-core forms keep their tables only as the tiled image).  By
+ * reciprocity (G(r,r') = G(r',r)^T, invoked by the paper for the first-slot
+ * sum) A^T approximates A itself.  Asynchronous like lmfmm_matvec. */
+lmfmm_status lmfmm_matvec_transpose(lmfmm_ctx *ctx, const void *y, int dtype, void *out, void *stream);
+
+/* Phi = A^H y (device buffers of element type dtype): conj(A^T conj(y)) with
+ * the transposed operator above where the form has it (stats
+ * adjoint_transposed = 1); in the tensor-core forms the reciprocity identity
+ * A^H y = conj(A conj(y)) with the forward kernels.  Asynchronous. */
 lmfmm_status lmfmm_matvec_adjoint(lmfmm_ctx *ctx, const void *y, int dtype, void *Phi,
                                   void *stream);
+
+/* Vector-Jacobian product of the FP64 form for a real objective L of the field
+ * E = A(r) J: given J[N][3] and g = dL/dconj(E) [N][3] (DEVICE, element type
+ * dtype), writes gJ = A^H g (dtype; may be NULL) and gxyz[N][3] (DEVICE
+ * doubles, caller order; may be NULL) with
+ *     gxyz_j = Re sum_i conj(g_i) . dE_i/dr_j,
+ * the derivative of the operator with the tree, lists and quadrature rules
+ * held fixed: the local expansions at r_j (target role, L2P's functions
+ * differentiated), the multipole functions at r_j contracted with the
+ * transposed pass's expansions (source role), and the near-field integrals
+ * differentiated in rho, phi and the image heights.  Runs a forward pass and
+ * the transposed pass, checkpointing the forward local expansions and
+ * helical charges in between.  The first call allocates the checkpoints and
+ * 20 derivative integrals per near point pair.  LMFMM_ERR_UNSUPPORTED outside
+ * the FP64 form.  Asynchronous on stream. */
+lmfmm_status lmfmm_gradient(lmfmm_ctx *ctx, const void *J, const void *g, int dtype, void *gJ, double *gxyz,
+                            void *stream);
 
 /* Waits for `stream` and reads the context's device status word, which every
  * matvec clears (stream-ordered) before its first kernel.  Returns LMFMM_OK,
@@ -233,6 +280,19 @@ lmfmm_status lmfmm_m2l_table(lmfmm_ctx *ctx, int l, int lp, int tgt_up, int src_
  * coefficients, so small entries are accurate relative to their own size. */
 lmfmm_status lmfmm_translation_matrix(int p, lmfmm_c128 k, const double *t, lmfmm_c128 *m2m,
                                       lmfmm_c128 *l2l);
+
+/* Host-only (no device, no context): the free-space M2L of the FMM's free
+ * part (Section 2, eq. maxwell_M2L_freespace with the Hessian of eq.
+ * GEandGH) between a source box centre c_s and a target centre c_t with
+ * c_s - c_t = (rho, 0, dz), wavenumber k, as the library stores it: tables
+ * [5][P][P] in the five-table form of lmfmm_m2l_table (same order, row =
+ * target index, column = source index, P = (p+1)^2), so that the M2L kernels
+ * apply it with the reaction tables' per-pair factors; blocks [3][3][P][P]
+ * (optional, NULL to skip) the full operator from the helical multipole
+ * expansions (a, b, c) to the helical local expansions of the field at this
+ * azimuth.  Caller-owned host arrays; 1 <= p <= 16. */
+lmfmm_status lmfmm_free_m2l_table(int p, lmfmm_c128 k, double rho, double dz, lmfmm_c128 *tables,
+                                   lmfmm_c128 *blocks);
 
 lmfmm_status lmfmm_get_stats(const lmfmm_ctx *ctx, lmfmm_stats *out);
 

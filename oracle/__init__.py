@@ -58,6 +58,9 @@ def _load():
             lib.or_direct.argtypes = [c_int, D, D, ctypes.c_int64, D, D, ctypes.c_int64, I64,
                                       ctypes.c_int64, I64, c_dbl, c_int, D]
             lib.or_direct.restype = ctypes.c_long
+            lib.or_direct_free.argtypes = [c_int, D, D, ctypes.c_int64, D, D, ctypes.c_int64, I64,
+                                           ctypes.c_int64, I64, c_int, D]
+            lib.or_direct_free.restype = None
             lib.or_legendre.argtypes = [c_int, c_dbl, c_dbl, c_dbl, c_dbl, D]
             lib.or_m2l_table.argtypes = [c_int, D, D, c_int, c_int, c_int, c_int, c_int, c_int,
                                          c_int, c_int, c_dbl, c_dbl, c_dbl, c_dbl, D]
@@ -188,6 +191,26 @@ def direct(d, k, xyz, J, targets=None, sources=None, rtol=1e-10, nthreads=0):
                           t.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), ns, sp,
                           float(rtol), int(nthreads), _dp(phi))
     return phi.reshape(-1, 3, 2) @ np.array([1.0, 1j]), n
+
+
+def direct_free(d, k, xyz, J, targets=None, sources=None, nthreads=0):
+    """Free-space part Phi^f_i = sum_{j != i, same layer} G_E^f(r_i, r_j) J_j
+    (closed-form dyad) for i in ``targets`` (all if None), j in ``sources``."""
+    L, d, kri = _medium(d, k)
+    xyz = np.ascontiguousarray(xyz, float)
+    N = xyz.shape[0]
+    q = np.ascontiguousarray(np.stack([J.real, J.imag], -1).reshape(-1))
+    t = np.arange(N, dtype=np.int64) if targets is None else np.ascontiguousarray(targets, np.int64)
+    phi = np.zeros(6 * t.size)
+    if sources is None:
+        sp, ns = None, 0
+    else:
+        s = np.ascontiguousarray(sources, np.int64)
+        sp, ns = s.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), s.size
+    _load().or_direct_free(L, _dp(d), _dp(kri), N, _dp(xyz), _dp(q), t.size,
+                           t.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), ns, sp, int(nthreads),
+                           _dp(phi))
+    return phi.reshape(-1, 3, 2) @ np.array([1.0, 1j])
 
 
 def legendre(nmax, cosb, sinb):

@@ -804,6 +804,45 @@ long or_direct(int L, const double *d, const double *kri, int64_t N, const doubl
     return total;
 }
 
+/*
+ * Free-space part of the same sum (eq. layeredmediafields): for each target
+ * i, Phi^f_i = sum_j G_E^f(r_i, r_j) q_j over the sources j != i in the layer
+ * of r_i, with the closed-form dyad of or_gfree at that layer's wavenumber.
+ * Same argument conventions as or_direct.
+ */
+void or_direct_free(int L, const double *d, const double *kri, int64_t N, const double *xyz,
+                    const double *q, int64_t nt, const int64_t *tidx, int64_t ns,
+                    const int64_t *sidx, int nthreads, double *phi)
+{
+    or_medium m;
+    make_medium(&m, L, d, kri);
+    int64_t nsrc = sidx ? ns : N;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 4)
+#endif
+    for (int64_t t = 0; t < nt; ++t) {
+        int64_t i = tidx[t];
+        int li = or_layer_of(m.L, m.d, xyz[3 * i + 2]);
+        cplx acc[3] = {0, 0, 0};
+        for (int64_t s = 0; s < nsrc; ++s) {
+            int64_t j = sidx ? sidx[s] : s;
+            if (j == i || or_layer_of(m.L, m.d, xyz[3 * j + 2]) != li) continue;
+            double G[18];
+            or_gfree(creal(m.k[li]), cimag(m.k[li]), xyz + 3 * i, xyz + 3 * j, G);
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) {
+                    cplx g = G[2 * (3 * a + b)] + I * G[2 * (3 * a + b) + 1];
+                    acc[a] += g * (q[6 * j + 2 * b] + I * q[6 * j + 2 * b + 1]);
+                }
+        }
+        for (int a = 0; a < 3; ++a) {
+            phi[6 * t + 2 * a] = creal(acc[a]);
+            phi[6 * t + 2 * a + 1] = cimag(acc[a]);
+        }
+    }
+}
+
 /* --------------------------------------------------- Legendre functions */
 
 /* Normalised associated Legendre functions with Condon-Shortley phase,

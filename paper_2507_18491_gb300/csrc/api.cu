@@ -35,10 +35,13 @@ struct DevState {
     M2LWork *m2lwork = nullptr;
     int64_t n_m2lwork = 0;
     void *tup = nullptr, *tdn = nullptr;   // [ngroup][P][P], complex T (scaled)
+    void *tupT = nullptr, *tdnT = nullptr; // their transposes (SIMT forms: the transposed operator)
     int64_t *tchild = nullptr, *tparent = nullptr;
     GemmWork *gwork = nullptr;
     std::vector<int64_t> gwork_off;  // per child level: [off[l], off[l+1])
-    void *tupi = nullptr, *tdni = nullptr;    // persistent kernel: tiled translation matrices (bf16 x 3)
+    void *tupi = nullptr, *tdni = nullptr;    // persistent kernel: tiled translation matrices (fp16 x 2)
+    float *tsc_up = nullptr, *tsc_dn = nullptr;   // ... and their row / column scales
+    float *tscale = nullptr;                  // persistent kernel: row / column scales of the table image
     M2LWork *twork = nullptr;        // persistent kernel: translation items, per child level
     bool trans_tc = false;           // M2M / L2L on the persistent kernel (tensor_cores = 3)
     std::vector<int64_t> twork_off;
@@ -46,6 +49,15 @@ struct DevState {
     cd *s2t = nullptr;               // near field: 8 combined coefficients per point pair
     S2TRow *s2twork = nullptr;       // near-field target rows
     int64_t n_s2twork = 0;
+    S2TRowT *s2tworkT = nullptr;     // transposed near field: (near pair, source) rows
+    int64_t n_s2tworkT = 0;
+    int64_t *fpairs = nullptr;       // free-space near leaf pairs [n][2] (source, target)
+    S2TRowT *frows = nullptr, *frowsT = nullptr;   // ... by target / by source point
+    int64_t n_frows = 0, n_frowsT = 0;
+    // position gradient (allocated by the first lmfmm_gradient call): checkpoints
+    // of the forward pass's local expansions and helical charges, a field buffer,
+    // and 20 derivative integrals per near point pair
+    cd *le_ck = nullptr, *qh_ck = nullptr, *gfield = nullptr, *s2tg = nullptr;
     int *flag = nullptr;
     int *mvstatus = nullptr;         // matvec status word (bit 4: tensor-core wait gave up)
     int m2l_kernel = 0;              // 0 FP64 SIMT, 1 FP32 SIMT, 2 tcgen05 streamed, 3 tcgen05 persistent
@@ -273,6 +285,7 @@ lmfmm_status lmfmm_default_params(lmfmm_params *prm)
     prm->precision = LMFMM_FP64;
     prm->tensor_cores = 1;
     prm->quad_node_cap = 1 << 20;
+    prm->components = LMFMM_REACTION;
     return LMFMM_OK;
 }
 
@@ -295,6 +308,10 @@ lmfmm_status lmfmm_create(lmfmm_ctx **out, const lmfmm_params *prm, int device)
     }
     if (prm->tensor_cores < 0 || prm->tensor_cores > 3) {
         g_err = "lmfmm_create: tensor_cores must be 0, 1, 2 or 3";
+        return LMFMM_ERR_ARG;
+    }
+    if (prm->components < LMFMM_REACTION || prm->components > LMFMM_TOTAL) {
+        g_err = "lmfmm_create: components must be LMFMM_REACTION, LMFMM_FREE or LMFMM_TOTAL";
         return LMFMM_ERR_ARG;
     }
     if (prm->quad_node_cap < 64) {
@@ -469,6 +486,16 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
         const CompDev &c = ctx->comps[g.comp];
         GeomDev gd{};
         gd.comp = g.comp;
+        if (i >= ctx->n_react_geoms) {
+            // free-space table: built on the host (addition theorem), not tabulated
+            gd.rho = g.rho;
+            gd.zs = g.zs;
+            gd.zt = g.zt;
+            gd.scale_s = gd.scale_t = kabs(c.l) * lev_size(g.level);
+            gd.tab_index = (int64_t)i;
+            hg[i] = gd;
+            continue;
+        }
         gd.src_primary = std::hypot(ctx->med.k[c.l].x, ctx->med.k[c.l].y) <=
                          std::hypot(ctx->med.k[c.lp].x, ctx->med.k[c.lp].y);
         gd.rho = g.rho;
@@ -490,12 +517,19 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
         // FP64 Chebyshev tabulation, then level scaling (and cast for the mixed form)
         cd *tab64 = nullptr;
         TRY(dalloc(ctx, &tab64, ctx->geoms.size() * (size_t)NTAB * P * P));
-        TRY(tabulate(ctx, hg, d->comps, dG, dcg, tab64, st, &ms_tab));
+        if (ctx->n_react_geoms > 0) {
+            std::vector<GeomDev> hr(hg.begin(), hg.begin() + ctx->n_react_geoms);
+            TRY(tabulate(ctx, hr, d->comps, dG, dcg, tab64, st, &ms_tab));
+        }
+        if (!ctx->free_tables.empty())
+            CK(cudaMemcpy(tab64 + ctx->n_react_geoms * (size_t)NTAB * P * P, ctx->free_tables.data(),
+                          ctx->free_tables.size() * sizeof(cd), cudaMemcpyHostToDevice));
         TRY(dupload(ctx, &d->geoms, hg));
         if (d->m2l_kernel == 3) {
             unsigned char *img = nullptr;
             TRY(dalloc(ctx, &img, m2l_tc2_image_bytes(p, (int64_t)hg.size())));
-            launch_tile_tables(p, 0, (int64_t)hg.size(), d->geoms, d->comps, tab64, img, st);
+            TRY(dalloc(ctx, &d->tscale, m2l_tc2_scale_floats(p, (int64_t)hg.size() * NTAB)));
+            launch_tile_tables(p, 0, (int64_t)hg.size(), d->geoms, d->comps, tab64, img, d->tscale, st);
             CK(cudaGetLastError());
             CK(cudaStreamSynchronize(st));
             dfree(ctx, tab64);
@@ -584,23 +618,48 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
                     V[r * P + c] = fd * V[r * P + c];
                 }
         }
+        // the SIMT forms also keep the transposes (the transposed operator runs on them)
+        const bool want_tr = d->m2l_kernel <= 1;
+        std::vector<cd> hupT, hdnT;
+        if (want_tr) {
+            hupT.resize(hup.size());
+            hdnT.resize(hdn.size());
+            for (size_t i = 0; i < ngr; ++i)
+                for (int r = 0; r < P; ++r)
+                    for (int c = 0; c < P; ++c) {
+                        hupT[i * P * P + (size_t)c * P + r] = hup[i * P * P + (size_t)r * P + c];
+                        hdnT[i * P * P + (size_t)c * P + r] = hdn[i * P * P + (size_t)r * P + c];
+                    }
+        }
         if (f32) {
-            std::vector<cf> u32(hup.size()), d32(hdn.size());
-            for (size_t i = 0; i < hup.size(); ++i) {
-                u32[i] = cf{(float)hup[i].x, (float)hup[i].y};
-                d32[i] = cf{(float)hdn[i].x, (float)hdn[i].y};
-            }
+            auto to32 = [](const std::vector<cd> &a) {
+                std::vector<cf> o(a.size());
+                for (size_t i = 0; i < a.size(); ++i) o[i] = cf{(float)a[i].x, (float)a[i].y};
+                return o;
+            };
             cf *a1 = nullptr, *a2 = nullptr;
-            TRY(dupload(ctx, &a1, u32));
-            TRY(dupload(ctx, &a2, d32));
+            TRY(dupload(ctx, &a1, to32(hup)));
+            TRY(dupload(ctx, &a2, to32(hdn)));
             d->tup = a1;
             d->tdn = a2;
+            if (want_tr) {
+                TRY(dupload(ctx, &a1, to32(hupT)));
+                TRY(dupload(ctx, &a2, to32(hdnT)));
+                d->tupT = a1;
+                d->tdnT = a2;
+            }
         } else {
             cd *a1 = nullptr, *a2 = nullptr;
             TRY(dupload(ctx, &a1, hup));
             TRY(dupload(ctx, &a2, hdn));
             d->tup = a1;
             d->tdn = a2;
+            if (want_tr) {
+                TRY(dupload(ctx, &a1, hupT));
+                TRY(dupload(ctx, &a2, hdnT));
+                d->tupT = a1;
+                d->tdnT = a2;
+            }
         }
         TRY(dupload(ctx, &d->tchild, ctx->tpair_child));
         TRY(dupload(ctx, &d->tparent, ctx->tpair_parent));
@@ -608,15 +667,18 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
         if (d->trans_tc) {
             // M2M / L2L on the persistent tensor-core kernel: tiled bf16 three-piece
             // images of the scaled FP64 matrices, items of 21 pairs (63 helical columns)
-            const size_t mw = tc2_matrix_bytes(p) / 4;
+            const size_t mw = tc2_matrix_bytes(p) / 4, ns = m2l_tc2_scale_floats(p, 1);
             std::vector<uint32_t> iu(ngr * mw), id(ngr * mw);
+            std::vector<float> su(ngr * ns), sd(ngr * ns);
             for (size_t i = 0; i < ngr; ++i) {
-                tile_matrix_tc2(p, &hup[i * P * P], &iu[i * mw]);
-                tile_matrix_tc2(p, &hdn[i * P * P], &id[i * mw]);
+                tile_matrix_tc2(p, &hup[i * P * P], &iu[i * mw], &su[i * ns]);
+                tile_matrix_tc2(p, &hdn[i * P * P], &id[i * mw], &sd[i * ns]);
             }
             uint32_t *a1 = nullptr, *a2 = nullptr;
             TRY(dupload(ctx, &a1, iu));
             TRY(dupload(ctx, &a2, id));
+            TRY(dupload(ctx, &d->tsc_up, su));
+            TRY(dupload(ctx, &d->tsc_dn, sd));
             d->tupi = a1;
             d->tdni = a2;
             std::vector<M2LWork> tw;
@@ -678,6 +740,29 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
         }
         TRY(dupload(ctx, &d->s2twork, sw));
         d->n_s2twork = (int64_t)sw.size();
+        std::vector<S2TRowT> swT;
+        for (size_t i = 0; i < ctx->near.size(); ++i) {
+            const Box &bs = ctx->boxes[ctx->near[i].src];
+            for (int64_t jj = 0; jj < bs.p1 - bs.p0; ++jj) swT.push_back(S2TRowT{(int64_t)i, (int)jj, 0});
+        }
+        TRY(dupload(ctx, &d->s2tworkT, swT));
+        d->n_s2tworkT = (int64_t)swT.size();
+        // free-space near field
+        std::vector<int64_t> fp;
+        std::vector<S2TRowT> fr, frT;
+        for (size_t i = 0; i < ctx->free_near.size(); ++i) {
+            const auto &pr = ctx->free_near[i];
+            fp.push_back(pr.first);
+            fp.push_back(pr.second);
+            const Box &bs = ctx->boxes[pr.first], &bt = ctx->boxes[pr.second];
+            for (int64_t ii = 0; ii < bt.p1 - bt.p0; ++ii) fr.push_back(S2TRowT{(int64_t)i, (int)ii, 0});
+            for (int64_t jj = 0; jj < bs.p1 - bs.p0; ++jj) frT.push_back(S2TRowT{(int64_t)i, (int)jj, 0});
+        }
+        TRY(dupload(ctx, &d->fpairs, fp));
+        TRY(dupload(ctx, &d->frows, fr));
+        TRY(dupload(ctx, &d->frowsT, frT));
+        d->n_frows = (int64_t)fr.size();
+        d->n_frowsT = (int64_t)frT.size();
     }
     TRY(check_flag(ctx));
     ctx->built = true;
@@ -686,7 +771,7 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
     S = lmfmm_stats{};
     S.n_points = N;
     S.n_layers = ctx->med.L + 1;
-    S.n_components = (int)ctx->comps.size();
+    S.n_components = ctx->n_react_comps;
     S.depth = ctx->depth;
     S.n_boxes = nbox;
     S.n_m2l_pairs = (int64_t)ctx->m2l.size();
@@ -699,9 +784,12 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
     S.ms_setup = std::chrono::duration<double, std::milli>(t1 - t0).count();
     S.m2l_columns = ncols;
     S.m2l_kernel = d->m2l_kernel;
-    for (const Geom &g : ctx->geoms)
-        if (ctx->comps[g.comp].l == ctx->comps[g.comp].lp) ++S.n_geometries_same_layer;
+    for (size_t i = 0; i < ctx->n_react_geoms; ++i)
+        if (ctx->comps[ctx->geoms[i].comp].l == ctx->comps[ctx->geoms[i].comp].lp) ++S.n_geometries_same_layer;
+    S.n_free_geometries = (int64_t)(ctx->geoms.size() - ctx->n_react_geoms);
+    S.n_free_near_point_pairs = ctx->n_free_pp;
     S.ms_tabulate = ms_tab;
+    S.adjoint_transposed = d->m2l_kernel <= 1;
     S.tab_flops = 8.0 * (double)qtot * NTAB * 16 * (p + 2) * (2 * p + 3) +
                   8.0 * (double)ctx->geoms.size() * NTAB * (double)P * P * (p + 2);
     return LMFMM_OK;
@@ -730,7 +818,7 @@ static lmfmm_status matvec_t(lmfmm_ctx *ctx, const void *J, int dtype, void *Phi
         if constexpr (std::is_same<T, float>::value) {
             if (d->trans_tc) {
                 int64_t w0 = d->twork_off[lev], w1 = d->twork_off[lev + 1];
-                CK(launch_trans_tc2(p, w1 - w0, d->twork + w0, d->tchild, d->tparent, d->tupi, me, me,
+                CK(launch_trans_tc2(p, w1 - w0, d->twork + w0, d->tchild, d->tparent, d->tupi, d->tsc_up, me, me,
                                     d->yscr, d->nsm, d->mvstatus, st));
                 nl += w1 > w0;
                 continue;
@@ -746,7 +834,7 @@ static lmfmm_status matvec_t(lmfmm_ctx *ctx, const void *J, int dtype, void *Phi
     CK(cudaMemsetAsync(le, 0, (size_t)nbox * 3 * P * sizeof(cx<T>), st));
     if constexpr (std::is_same<T, float>::value) {
         if (d->m2l_kernel == 3) {
-            CK(launch_m2l_tc2(p, d->n_m2lwork, d->m2lwork, d->geoms, d->m2l, d->ephase, d->tab,
+            CK(launch_m2l_tc2(p, d->n_m2lwork, d->m2lwork, d->geoms, d->m2l, d->ephase, d->tab, d->tscale,
                               me, le, d->yscr, d->nsm, d->mvstatus, st));
         }
         else if (d->m2l_kernel == 2)
@@ -764,7 +852,7 @@ static lmfmm_status matvec_t(lmfmm_ctx *ctx, const void *J, int dtype, void *Phi
         if constexpr (std::is_same<T, float>::value) {
             if (d->trans_tc) {
                 int64_t w0 = d->twork_off[lev], w1 = d->twork_off[lev + 1];
-                CK(launch_trans_tc2(p, w1 - w0, d->twork + w0, d->tparent, d->tchild, d->tdni, le, le,
+                CK(launch_trans_tc2(p, w1 - w0, d->twork + w0, d->tparent, d->tchild, d->tdni, d->tsc_dn, le, le,
                                     d->yscr, d->nsm, d->mvstatus, st));
                 nl += w1 > w0;
                 continue;
@@ -780,6 +868,8 @@ static lmfmm_status matvec_t(lmfmm_ctx *ctx, const void *J, int dtype, void *Phi
     launch_l2p<T>(p, d->nleaves, d->leaves, d->boxes, d->xyz, le, ctx->med, d->lscale, d->ph, st);
     CK(cudaEventRecord(d->ev[5], st));
     launch_s2t_apply8(d->n_s2twork, d->s2twork, d->near, d->boxes, d->s2t, d->qh, d->ph, st);
+    launch_p2p_free(d->n_frows, d->frows, d->fpairs, d->boxes, d->xyz, ctx->med, d->qh, d->ph, false, st);
+    nl += d->n_frows > 0;
     CK(cudaEventRecord(d->ev[6], st));
     launch_scatter_out(N, d->perm, d->ph, Phi, dtype, cj, st);
     nl += (d->nleaves > 0) + (d->n_s2twork > 0) + (N > 0);   // L2P, near field, scatter
@@ -788,6 +878,70 @@ static lmfmm_status matvec_t(lmfmm_ctx *ctx, const void *J, int dtype, void *Phi
     d->mv_recorded = true;
     ctx->stats.launches = nl;
     return LMFMM_OK;
+}
+
+// The transposed operator A^T = G^T (P2M^T M2M^T M2L^T L2L^T L2P^T + S2T^T) S^T,
+// every factor the exact transpose of the forward one (SIMT forms): L2P^T sums
+// the point values against L2P's functions (P2M's kernel), L2L^T and M2M^T run
+// the transposed matrices up and down the tree, M2L^T applies the transposed
+// tables, P2M^T evaluates with P2M's functions (L2P's kernel).  With cj the
+// input and output are conjugated: conj(A^T conj y) = A^H y.
+template <typename T>
+static lmfmm_status matvec_tr_t(lmfmm_ctx *ctx, const void *y, int dtype, void *out, cudaStream_t st, bool cj)
+{
+    DevState *d = DS(ctx);
+    const int p = ctx->prm.p, P = (p + 1) * (p + 1);
+    const int64_t N = ctx->N, nbox = (int64_t)ctx->boxes.size();
+    cx<T> *me = (cx<T> *)d->me, *le = (cx<T> *)d->le;
+    const cx<T> *tupT = (const cx<T> *)d->tupT, *tdnT = (const cx<T> *)d->tdnT;
+    int nl = 0;
+    CK(cudaEventRecord(d->ev[0], st));
+    CK(cudaMemsetAsync(d->mvstatus, 0, sizeof(int), st));
+    launch_gather_tr(N, d->perm, y, dtype, d->ph, cj, st);   // ph <- S^T y
+    CK(cudaMemsetAsync(le, 0, (size_t)nbox * 3 * P * sizeof(cx<T>), st));
+    launch_p2m<T>(p, d->nleaves, d->leaves, d->boxes, d->xyz, d->ph, ctx->med, d->lscale, le, st, true);
+    nl += (N > 0) + (d->nleaves > 0);
+    CK(cudaEventRecord(d->ev[1], st));
+    for (int lev = ctx->depth; lev >= 1; --lev) {   // L2L^T: children into parents
+        int64_t w0 = d->gwork_off[lev], w1 = d->gwork_off[lev + 1];
+        launch_group_gemm_t<T>(p, w1 - w0, d->gwork + w0, tdnT, d->tchild, d->tparent, le, le, true, st);
+        nl += w1 > w0;
+    }
+    CK(cudaEventRecord(d->ev[2], st));
+    CK(cudaMemsetAsync(me, 0, (size_t)nbox * 3 * P * sizeof(cx<T>), st));
+    launch_m2l_tr<T>(p, d->n_m2lwork, d->m2lwork, d->geoms, d->comps, d->m2l, (const cx<T> *)d->tab, le, me, st);
+    nl += d->n_m2lwork > 0;
+    CK(cudaEventRecord(d->ev[3], st));
+    for (int lev = 1; lev <= ctx->depth; ++lev) {   // M2M^T: parents into children
+        int64_t w0 = d->gwork_off[lev], w1 = d->gwork_off[lev + 1];
+        launch_group_gemm_t<T>(p, w1 - w0, d->gwork + w0, tupT, d->tparent, d->tchild, me, me, true, st);
+        nl += w1 > w0;
+    }
+    CK(cudaEventRecord(d->ev[4], st));
+    launch_l2p<T>(p, d->nleaves, d->leaves, d->boxes, d->xyz, me, ctx->med, d->lscale, d->qh, st, true, false);
+    CK(cudaEventRecord(d->ev[5], st));
+    launch_s2t_apply8_tr(d->n_s2tworkT, d->s2tworkT, d->near, d->boxes, d->s2t, d->ph, d->qh, st);
+    launch_p2p_free(d->n_frowsT, d->frowsT, d->fpairs, d->boxes, d->xyz, ctx->med, d->ph, d->qh, true, st);
+    nl += d->n_frowsT > 0;
+    CK(cudaEventRecord(d->ev[6], st));
+    launch_scatter_tr(N, d->perm, d->qh, out, dtype, cj, st);
+    nl += (d->nleaves > 0) + (d->n_s2tworkT > 0) + (N > 0);
+    CK(cudaEventRecord(d->ev[7], st));
+    CK(cudaGetLastError());
+    d->mv_recorded = true;
+    ctx->stats.launches = nl;
+    return LMFMM_OK;
+}
+
+static lmfmm_status matvec_tr_impl(lmfmm_ctx *ctx, const void *y, int dtype, void *out, cudaStream_t st, bool cj)
+{
+    if (DS(ctx)->m2l_kernel > 1) {
+        ctx->err = "the transposed operator runs in the FP64 form and the mixed form with tensor_cores = 0 "
+                   "(the tensor-core forms hold their tables only as the tiled image)";
+        return LMFMM_ERR_UNSUPPORTED;
+    }
+    if (ctx->prm.precision == LMFMM_MIXED) return matvec_tr_t<float>(ctx, y, dtype, out, st, cj);
+    return matvec_tr_t<double>(ctx, y, dtype, out, st, cj);
 }
 
 static lmfmm_status matvec_impl(lmfmm_ctx *ctx, const void *J, int dtype, void *Phi,
@@ -828,7 +982,16 @@ lmfmm_status lmfmm_matvec_adjoint(lmfmm_ctx *ctx, const void *y, int dtype, void
     if (!ctx) return LMFMM_ERR_ARG;
     TRY(matvec_args(ctx, "matvec_adjoint", y, dtype, Phi));
     CK(cudaSetDevice(ctx->device));
+    if (DS(ctx)->m2l_kernel <= 1) return matvec_tr_impl(ctx, y, dtype, Phi, (cudaStream_t)stream, true);
     return matvec_impl(ctx, y, dtype, Phi, (cudaStream_t)stream, true);
+}
+
+lmfmm_status lmfmm_matvec_transpose(lmfmm_ctx *ctx, const void *y, int dtype, void *out, void *stream)
+{
+    if (!ctx) return LMFMM_ERR_ARG;
+    TRY(matvec_args(ctx, "matvec_transpose", y, dtype, out));
+    CK(cudaSetDevice(ctx->device));
+    return matvec_tr_impl(ctx, y, dtype, out, (cudaStream_t)stream, false);
 }
 
 lmfmm_status lmfmm_matvec_host(lmfmm_ctx *ctx, const void *J, int dtype, void *Phi, void *stream)
@@ -846,6 +1009,51 @@ lmfmm_status lmfmm_matvec_host(lmfmm_ctx *ctx, const void *J, int dtype, void *P
     TRY(matvec_impl(ctx, sin, dtype, sout, st, false));
     CK(cudaMemcpyAsync(Phi, sout, bytes, cudaMemcpyDeviceToHost, st));
     return check_mvstatus(ctx, st);
+}
+
+lmfmm_status lmfmm_gradient(lmfmm_ctx *ctx, const void *J, const void *g, int dtype, void *gJ, double *gxyz,
+                            void *stream)
+{
+    if (!ctx) return LMFMM_ERR_ARG;
+    TRY(matvec_args(ctx, "gradient", J, dtype, g));
+    if (!gJ && !gxyz) {
+        ctx->err = "gradient: nothing to compute (gJ and gxyz are NULL)";
+        return LMFMM_ERR_ARG;
+    }
+    if (ctx->prm.precision != LMFMM_FP64 || ctx->prm.components != LMFMM_REACTION) {
+        ctx->err = "gradient: the position gradient runs in the FP64 form of the reaction part";
+        return LMFMM_ERR_UNSUPPORTED;
+    }
+    CK(cudaSetDevice(ctx->device));
+    DevState *d = DS(ctx);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int p = ctx->prm.p, P = (p + 1) * (p + 1);
+    const int64_t N = ctx->N, nbox = (int64_t)ctx->boxes.size();
+    if (!d->le_ck) {
+        TRY(dalloc(ctx, &d->le_ck, (size_t)nbox * 3 * P));
+        TRY(dalloc(ctx, &d->qh_ck, (size_t)N * 3));
+        TRY(dalloc(ctx, &d->gfield, (size_t)N * 3));
+        TRY(dalloc(ctx, &d->s2tg, (size_t)std::max<int64_t>(1, ctx->n_near_pp) * 20));
+        launch_s2t_pre_grad((int64_t)ctx->near.size(), d->near, d->boxes, d->xyz, ctx->med, d->comps,
+                            medium_a(ctx->med), ctx->prm.quad_node_cap, d->s2tg, st);
+        CK(cudaGetLastError());
+    }
+    // forward pass (its result is not needed), then checkpoint what the
+    // transposed pass overwrites: the local expansions and the helical charges
+    TRY(matvec_t<double>(ctx, J, dtype, d->gfield, st, false));
+    CK(cudaMemcpyAsync(d->le_ck, d->le, (size_t)nbox * 3 * P * sizeof(cd), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(d->qh_ck, d->qh, (size_t)N * 3 * sizeof(cd), cudaMemcpyDeviceToDevice, st));
+    // transposed pass of conj(g): gJ = A^H g; leaves ph = S^T conj(g), me = its multipole expansions
+    TRY(matvec_tr_t<double>(ctx, g, dtype, gJ ? gJ : (void *)d->gfield, st, true));
+    if (gxyz) {
+        CK(cudaMemsetAsync(gxyz, 0, (size_t)N * 3 * sizeof(double), st));
+        launch_grad_leaf(p, N, d->nleaves, d->leaves, d->boxes, d->xyz, d->perm, d->le_ck, (const cd *)d->me,
+                         d->qh_ck, d->ph, ctx->med, d->lscale, gxyz, st);
+        launch_grad_near((int64_t)ctx->near.size(), d->near, d->boxes, d->xyz, d->perm, d->comps, d->s2tg,
+                         d->qh_ck, d->ph, gxyz, st);
+        CK(cudaGetLastError());
+    }
+    return LMFMM_OK;
 }
 
 lmfmm_status lmfmm_check(lmfmm_ctx *ctx, void *stream)
@@ -891,9 +1099,9 @@ lmfmm_status lmfmm_direct(lmfmm_ctx *ctx, const lmfmm_c128 *J, lmfmm_c128 *Phi, 
     cudaStream_t st = (cudaStream_t)stream;
     // every (component, source leaf, target leaf) pair is treated as near
     int64_t npp = 0, cnt = 0;
-    for (const CompDev &c : ctx->comps)
-        cnt += (ctx->lvl1[c.l][ctx->depth] - ctx->lvl0[c.l][ctx->depth]) *
-               (ctx->lvl1[c.lp][ctx->depth] - ctx->lvl0[c.lp][ctx->depth]);
+    for (int ci = 0; ci < ctx->n_react_comps; ++ci)
+        cnt += (ctx->lvl1[ctx->comps[ci].l][ctx->depth] - ctx->lvl0[ctx->comps[ci].l][ctx->depth]) *
+               (ctx->lvl1[ctx->comps[ci].lp][ctx->depth] - ctx->lvl0[ctx->comps[ci].lp][ctx->depth]);
     std::vector<NearPair> all((size_t)cnt);
     all_leaf_pairs(ctx, all.data(), cnt, &npp);
     NearPair *dn = nullptr;
@@ -1030,6 +1238,18 @@ lmfmm_status lmfmm_translation_matrix(int p, lmfmm_c128 k, const double *t, lmfm
     std::vector<double> gv;
     gaunt_table(p, goff, gl, gv);
     translation_matrix(p, zc(k.re, k.im), t, goff, gl, gv, (cd *)m2m, (cd *)l2l);
+    return LMFMM_OK;
+}
+
+lmfmm_status lmfmm_free_m2l_table(int p, lmfmm_c128 k, double rho, double dz, lmfmm_c128 *tables,
+                                   lmfmm_c128 *blocks)
+{
+    if (p < 1 || p > 16 || !tables || !(rho >= 0) || !std::isfinite(rho) || !std::isfinite(dz) ||
+        !(rho > 0 || dz != 0)) {
+        g_err = "free_m2l_table: bad argument";
+        return LMFMM_ERR_ARG;
+    }
+    free_m2l_tables(p, zc(k.re, k.im), rho, dz, (cd *)tables, (cd *)blocks);
     return LMFMM_OK;
 }
 

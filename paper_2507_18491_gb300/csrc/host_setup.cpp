@@ -9,6 +9,7 @@
 #include <map>
 #include <numeric>
 #include <tuple>
+#include <thread>
 #include <unordered_map>
 
 #include "internal.h"
@@ -198,7 +199,7 @@ lmfmm_status build_host_structures(lmfmm_ctx *ctx)
     for (int64_t i = 0; i < ctx->N; ++i) cnt[ctx->layer[i]]++;
     // components
     ctx->comps.clear();
-    if (L >= 1) {
+    if (L >= 1 && ctx->prm.components != LMFMM_FREE) {
         for (int l = 0; l <= L; ++l)
             for (int lp = 0; lp <= L; ++lp) {
                 if (!cnt[l] || !cnt[lp]) continue;
@@ -226,6 +227,7 @@ lmfmm_status build_host_structures(lmfmm_ctx *ctx)
                     }
             }
     }
+    ctx->n_react_comps = (int)ctx->comps.size();
     // dual-tree traversal
     const double theta = ctx->prm.theta, eta = ctx->prm.eta;
     struct PairRec { int comp, level; int64_t src, tgt; };
@@ -329,6 +331,14 @@ lmfmm_status build_host_structures(lmfmm_ctx *ctx)
         ctx->geoms[g].pair0 = off[g];
         ctx->geoms[g].pair1 = off[g + 1];
     }
+    ctx->n_react_geoms = ctx->geoms.size();
+    ctx->free_tables.clear();
+    ctx->free_near.clear();
+    ctx->n_free_pp = 0;
+    if (ctx->prm.components != LMFMM_REACTION) {
+        lmfmm_status fs = build_free_structures(ctx);
+        if (fs != LMFMM_OK) return fs;
+    }
     // translation groups (child level lev, octant from the child's key)
     ctx->tgroups.clear();
     ctx->tpair_child.clear();
@@ -366,7 +376,7 @@ int64_t all_leaf_pairs(const lmfmm_ctx *ctx, NearPair *out, int64_t cap, int64_t
 {
     int64_t np = 0, npp = 0;
     const int D = ctx->depth;
-    for (int ci = 0; ci < (int)ctx->comps.size(); ++ci) {
+    for (int ci = 0; ci < ctx->n_react_comps; ++ci) {
         const CompDev &c = ctx->comps[ci];
         for (int64_t bs = ctx->lvl0[c.l][D]; bs < ctx->lvl1[c.l][D]; ++bs)
             for (int64_t bt = ctx->lvl0[c.lp][D]; bt < ctx->lvl1[c.lp][D]; ++bt) {
@@ -694,6 +704,312 @@ void translation_matrix(int p, zc kk, const double t[3], const std::vector<int64
                     up[e] = cd{(double)u.real(), (double)u.imag()};
                     dn[e] = cd{(double)v.real(), (double)v.imag()};
                 }
+}
+
+}  // namespace lmf
+
+namespace lmf {
+
+// ------------------------------------------------------- free-space part
+// Section 2 (eqs. freespace3dmulexpscaled, melecoeffreescaled,
+// maxwell_M2L_freespace): the free-space part Phi^f = (I + grad grad / k^2) u,
+// u = sum_j g(r, r_j) J_j, over the sources of the target's own layer.  The
+// multipole expansion M_nm = 4 pi sum q j_n(k r) conj Y_nm is the one P2M
+// already forms, and u = (ik / 4 pi) sum M_nm h_n(k r) Y_nm outside the box.
+// The M2L re-expands the singular harmonics S_n^m = h_n Y_n^m about the
+// target centre with the addition theorem,
+//   S_n'^m'(rho + t) = sum SR_{nu mu, n' m'}(t) R_nu^mu(rho),  t = c_t - c_s,
+//   SR = i^(nu - n') 4 pi sum_l i^l h_l(k |t|) conj(Y_l^(mu - m')(t^)) G(l; n', nu),
+// G the Gaunt coefficient int Y_l^(mu-m') Y_n'^m' conj(Y_nu^mu), which is the
+// L2L construction with h_l in place of j_l.  The Hessian acts on the singular
+// coefficients exactly (d/dz and d/dx +- i d/dy map S_n^m to degrees n +- 1 with
+// the coefficients of the regular harmonics), so the helical field is
+//   A' = u_a + D+ w / k^2,  B' = u_b + D- w / k^2,  C' = u_c + d_z w / k^2,
+//   w = (D- u_a + D+ u_b) / 2 + d_z u_c,
+// whose nine blocks have the reaction M2L's structure (spin kappa = change of
+// the order m): they are stored as its five tables with the same per-pair
+// phase factors, so the M2L kernels apply them unchanged.
+
+namespace {
+
+// spherical Hankel functions h_0..h_L at complex z (upward recurrence, stable
+// for this dominant solution)
+void sph_hankel_ld(lz z, int L, std::vector<lz> &h)
+{
+    h.assign(L + 1, 0);
+    const lz iz(0, 1);
+    const lz e = std::exp(iz * z);
+    h[0] = -iz * e / z;
+    if (L >= 1) h[1] = -e * (z + iz) / (z * z);
+    for (int n = 1; n < L; ++n) h[n + 1] = (ld)(2 * n + 1) / z * h[n] - h[n - 1];
+}
+
+// Gaunt coefficients G(l; n', nu) = int Y_l^(mu-m') Y_n'^m' conj(Y_nu^mu) for
+// nu <= pout, n' <= pin, stored per (nu mu, n' m') as (l, value) runs
+void gaunt_rect(int pout, int pin, std::vector<int64_t> &off, std::vector<int> &lval, std::vector<double> &gval)
+{
+    const int Po = (pout + 1) * (pout + 1), Pi = (pin + 1) * (pin + 1);
+    const int lmax = pout + pin, nq = (pout + pin + lmax) / 2 + 2;
+    std::vector<ld> xq(nq), wq(nq);
+    for (int i = 0; i < nq; ++i) {
+        ld x = std::cos(3.14159265358979323846264338327950288L * (i + 0.75L) / (nq + 0.5L)), dp = 0;
+        for (int it = 0; it < 100; ++it) {
+            ld p0 = 1, p1 = x;
+            for (int n = 2; n <= nq; ++n) {
+                ld p2 = ((2 * n - 1) * x * p1 - (n - 1) * p0) / n;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = nq * (x * p1 - p0) / (x * x - 1);
+            ld dx = p1 / dp;
+            x -= dx;
+            if (std::fabs((double)dx) < 1e-22) break;
+        }
+        xq[i] = x;
+        wq[i] = 2.0L / ((1 - x * x) * dp * dp);
+    }
+    std::vector<std::vector<ld>> Pq(nq);
+    for (int q = 0; q < nq; ++q) legendre_ld(lmax, xq[q], std::sqrt(1 - xq[q] * xq[q]), Pq[q]);
+    const ld twopi = 2 * 3.14159265358979323846264338327950288L;
+    off.assign((size_t)Po * Pi + 1, 0);
+    lval.clear();
+    gval.clear();
+    for (int n = 0; n <= pout; ++n)
+        for (int m = -n; m <= n; ++m)
+            for (int n1 = 0; n1 <= pin; ++n1)
+                for (int m1 = -n1; m1 <= n1; ++m1) {
+                    const int mu = m - m1, amu = mu < 0 ? -mu : mu;
+                    for (int l = std::abs(n - n1); l <= n + n1; ++l) {
+                        if (((l + n + n1) & 1) || l < amu) continue;
+                        ld s = 0;
+                        for (int q = 0; q < nq; ++q)
+                            s += wq[q] * ptilde(Pq[q], l, mu) * ptilde(Pq[q], n1, m1) * ptilde(Pq[q], n, m);
+                        s *= twopi;
+                        if (std::fabs((double)s) < 1e-30) continue;
+                        lval.push_back(l);
+                        gval.push_back((double)s);
+                    }
+                    off[(size_t)nidx(n, m) * Pi + nidx(n1, m1) + 1] = (int64_t)lval.size();
+                }
+}
+
+// derivative maps on coefficient vectors c[n^2 + n + m] (n <= N) of expansions
+// in R_n^m or S_n^m: returns d/dz, D+ or D- (which = 0, 1, 2) of sum c R
+void deriv_apply(int which, int N, lz k, const std::vector<lz> &c, std::vector<lz> &o)
+{
+    o.assign(c.size(), 0);
+    auto sq = [](ld v) { return v > 0 ? std::sqrt(v) : (ld)0; };
+    for (int n = 0; n <= N; ++n)
+        for (int m = -n; m <= n; ++m) {
+            const lz v = c[nidx(n, m)];
+            if (v == lz(0)) continue;
+            auto add = [&](int nn, int mm, lz w) {
+                if (nn < 0 || nn > N || mm < -nn || mm > nn) return;
+                o[nidx(nn, mm)] += w * v;
+            };
+            const ld n2 = (ld)n;
+            if (which == 0) {
+                add(n - 1, m, k * sq((n2 * n2 - (ld)m * m) / ((2 * n2 - 1) * (2 * n2 + 1))));
+                add(n + 1, m, -k * sq(((n2 + 1) * (n2 + 1) - (ld)m * m) / ((2 * n2 + 1) * (2 * n2 + 3))));
+            } else if (which == 1) {
+                add(n + 1, m + 1, k * sq((n2 + m + 1) * (n2 + m + 2) / ((2 * n2 + 1) * (2 * n2 + 3))));
+                add(n - 1, m + 1, k * sq((n2 - m) * (n2 - m - 1) / ((2 * n2 - 1) * (2 * n2 + 1))));
+            } else {
+                add(n + 1, m - 1, -k * sq((n2 - m + 1) * (n2 - m + 2) / ((2 * n2 + 1) * (2 * n2 + 3))));
+                add(n - 1, m - 1, -k * sq((n2 + m) * (n2 + m - 1) / ((2 * n2 - 1) * (2 * n2 + 1))));
+            }
+        }
+}
+
+}  // namespace
+
+void free_m2l_tables(int p, zc kk, double rho, double dz, cd *out5, cd *blocks9)
+{
+    const int P = (p + 1) * (p + 1), p2 = p + 2, P2 = (p2 + 1) * (p2 + 1);
+    const lz k(kk.real(), kk.imag());
+    // Hessian blocks H[o][v]: input unit vector (degree <= p, component v) ->
+    // singular coefficients of the helical field component o (degree <= p + 2)
+    std::vector<lz> Hb((size_t)9 * P2 * P, 0);
+    auto H = [&](int o, int v, int r, int c) -> lz & { return Hb[((size_t)(3 * o + v) * P2 + r) * P + c]; };
+    const lz ik2 = (ld)1 / (k * k);
+    std::vector<lz> e(P2), d1, d2;
+    for (int c = 0; c < P; ++c) {
+        std::fill(e.begin(), e.end(), lz(0));
+        e[c] = 1;
+        // first derivatives of the unit input, then the second ones used below
+        std::vector<lz> dzv, dpv, dmv;
+        deriv_apply(0, p2, k, e, dzv);
+        deriv_apply(1, p2, k, e, dpv);
+        deriv_apply(2, p2, k, e, dmv);
+        // w contributions: from a: D- a / 2, from b: D+ b / 2, from c: d_z c
+        const std::vector<lz> *wv[3] = {&dmv, &dpv, &dzv};
+        const ld wf[3] = {0.5L, 0.5L, 1.0L};
+        for (int v = 0; v < 3; ++v) {
+            std::vector<lz> w(P2);
+            for (int r = 0; r < P2; ++r) w[r] = wf[v] * (*wv[v])[r];
+            std::vector<lz> gp, gm, gz;
+            deriv_apply(1, p2, k, w, gp);
+            deriv_apply(2, p2, k, w, gm);
+            deriv_apply(0, p2, k, w, gz);
+            for (int r = 0; r < P2; ++r) {
+                H(0, v, r, c) = ik2 * gp[r] + (v == 0 ? e[r] : lz(0));
+                H(1, v, r, c) = ik2 * gm[r] + (v == 1 ? e[r] : lz(0));
+                H(2, v, r, c) = ik2 * gz[r] + (v == 2 ? e[r] : lz(0));
+            }
+        }
+    }
+    // SR(t), t = c_t - c_s = (-rho, 0, -dz), rows nu <= p, columns n' <= p + 2
+    std::vector<int64_t> goff;
+    std::vector<int> gl;
+    std::vector<double> gv;
+    gaunt_rect(p, p2, goff, gl, gv);
+    const ld tx = -rho, tz = -dz, tn = std::sqrt(tx * tx + tz * tz);
+    std::vector<lz> hl;
+    sph_hankel_ld(k * tn, p + p2, hl);
+    std::vector<ld> Pt;
+    legendre_ld(p + p2, tz / tn, std::fabs(tx) / tn, Pt);
+    const ld phi = std::atan2((ld)0, tx);
+    const ld fourpi = 4 * 3.14159265358979323846264338327950288L;
+    std::vector<lz> SR((size_t)P * P2);
+    auto ip = [](int q) {
+        q = ((q % 4) + 4) % 4;
+        return q == 0 ? lz(1) : q == 1 ? lz(0, 1) : q == 2 ? lz(-1) : lz(0, -1);
+    };
+    for (int n = 0; n <= p; ++n)
+        for (int m = -n; m <= n; ++m)
+            for (int n1 = 0; n1 <= p2; ++n1)
+                for (int m1 = -n1; m1 <= n1; ++m1) {
+                    const size_t ge = (size_t)nidx(n, m) * P2 + nidx(n1, m1);
+                    const int mu = m - m1;
+                    lz s = 0;
+                    for (int64_t q = goff[ge]; q < goff[ge + 1]; ++q)
+                        s += ip(gl[q]) * hl[gl[q]] * ptilde(Pt, gl[q], mu) * (ld)gv[q];
+                    SR[ge] = ip(n - n1) * fourpi * std::polar((ld)1, -(ld)mu * phi) * s;
+                }
+    // T_ov = (ik / 4 pi) SR H_ov
+    const lz pre = lz(0, 1) * k / fourpi;
+    std::vector<lz> T((size_t)9 * P * P, 0);
+    for (int ov = 0; ov < 9; ++ov)
+        for (int r = 0; r < P; ++r)
+            for (int c = 0; c < P; ++c) {
+                lz acc = 0;
+                for (int q = 0; q < P2; ++q) {
+                    const lz h = Hb[((size_t)ov * P2 + q) * P + c];
+                    if (h != lz(0)) acc += SR[(size_t)r * P2 + q] * h;
+                }
+                T[((size_t)ov * P + r) * P + c] = pre * acc;
+            }
+    if (blocks9)
+        for (size_t i = 0; i < T.size(); ++i) blocks9[i] = cd{(double)T[i].real(), (double)T[i].imag()};
+    // the five tables: block (out, in) of each table's kappa >= 0 column divided by
+    // its factors coef i^(1+kappa) (-i)^(nu+mu) i^(n'+m') at phi = 0
+    const int to_out[5] = {0, 2, 0, 2, 0}, to_in[5] = {0, 2, 2, 1, 1}, kap[5] = {0, 0, 1, 1, 2};
+    const ld coef[5] = {0.5L, 1.0L, 1.0L, 0.5L, -0.5L};
+    std::vector<int> deg(P), ord(P);
+    for (int n = 0; n <= p; ++n)
+        for (int m = -n; m <= n; ++m) {
+            deg[nidx(n, m)] = n;
+            ord[nidx(n, m)] = m;
+        }
+    for (int t = 0; t < 5; ++t)
+        for (int r = 0; r < P; ++r)
+            for (int c = 0; c < P; ++c) {
+                const lz f = coef[t] * ip(1 + kap[t]) * ip(-(deg[r] + ord[r])) * ip(deg[c] + ord[c]);
+                const lz v = T[((size_t)(3 * to_out[t] + to_in[t]) * P + r) * P + c] / f;
+                out5[((size_t)t * P + r) * P + c] = cd{(double)v.real(), (double)v.imag()};
+            }
+}
+
+lmfmm_status build_free_structures(lmfmm_ctx *ctx)
+{
+    const int L = ctx->med.L, D = ctx->depth, p = ctx->prm.p, P = (p + 1) * (p + 1);
+    const double h = ctx->root_h, theta = ctx->prm.theta;
+    std::vector<int64_t> cnt(L + 1, 0);
+    for (int64_t i = 0; i < ctx->N; ++i) cnt[ctx->layer[i]]++;
+    struct PairRec { int comp, level; int64_t src, tgt; };
+    std::vector<PairRec> far;
+    std::vector<int> fcomp(L + 1, -1);
+    for (int l = 0; l <= L; ++l) {
+        if (!cnt[l]) continue;
+        // pseudo-component: same layer, no images, s = +1
+        CompDev c{};
+        c.l = c.lp = l;
+        c.s = 1.0;
+        fcomp[l] = (int)ctx->comps.size();
+        ctx->comps.push_back(c);
+        std::vector<std::pair<int64_t, int64_t>> stack{{ctx->lvl0[l][0], ctx->lvl0[l][0]}};
+        while (!stack.empty()) {
+            auto [bs, bt] = stack.back();
+            stack.pop_back();
+            const Box &B = ctx->boxes[bs], &C = ctx->boxes[bt];
+            const double dx = B.c[0] - C.c[0], dy = B.c[1] - C.c[1], dzz = B.c[2] - C.c[2];
+            const double R = std::sqrt(dx * dx + dy * dy + dzz * dzz);
+            if (bs != bt && B.r + C.r <= theta * R) {
+                far.push_back({fcomp[l], B.level, bs, bt});
+            } else if (B.level == D) {
+                ctx->free_near.push_back({bs, bt});
+                ctx->n_free_pp += (B.p1 - B.p0) * (C.p1 - C.p0);
+            } else {
+                for (int i = 0; i < B.nchild; ++i)
+                    for (int j = 0; j < C.nchild; ++j) stack.push_back({B.child0 + i, C.child0 + j});
+            }
+        }
+    }
+    // free geometries: (layer, level, rho^2 in cells, dz in cells)
+    std::map<std::tuple<int, int, int64_t, int>, int> gid;
+    std::vector<int> pg(far.size());
+    const size_t g0 = ctx->geoms.size();
+    for (size_t i = 0; i < far.size(); ++i) {
+        const Box &B = ctx->boxes[far[i].src], &C = ctx->boxes[far[i].tgt];
+        const int64_t ddx = B.ix - C.ix, ddy = B.iy - C.iy;
+        auto key = std::make_tuple(far[i].comp, far[i].level, ddx * ddx + ddy * ddy, B.iz - C.iz);
+        auto it = gid.find(key);
+        if (it == gid.end()) {
+            Geom g{};
+            g.comp = far[i].comp;
+            g.level = far[i].level;
+            const double Sl = 2.0 * h / (double)(1u << g.level);
+            g.rho = Sl * std::sqrt((double)(ddx * ddx + ddy * ddy));
+            g.zs = B.c[2];
+            g.zt = B.c[2] - Sl * (double)(B.iz - C.iz);
+            it = gid.emplace(key, (int)ctx->geoms.size()).first;
+            ctx->geoms.push_back(g);
+        }
+        pg[i] = it->second;
+    }
+    const size_t nfg = ctx->geoms.size() - g0;
+    std::vector<int64_t> off(nfg + 1, 0);
+    for (size_t i = 0; i < far.size(); ++i) off[pg[i] - g0 + 1]++;
+    for (size_t g = 0; g < nfg; ++g) off[g + 1] += off[g];
+    const int64_t base = (int64_t)ctx->m2l.size();
+    ctx->m2l.resize(base + far.size());
+    std::vector<int64_t> pos(off.begin(), off.end() - 1);
+    for (size_t i = 0; i < far.size(); ++i) {
+        const Box &B = ctx->boxes[far[i].src], &C = ctx->boxes[far[i].tgt];
+        const double dx = B.c[0] - C.c[0], dy = B.c[1] - C.c[1];
+        const double rr = std::sqrt(dx * dx + dy * dy);
+        ctx->m2l[base + pos[pg[i] - g0]++] = M2LPair{far[i].src, far[i].tgt, rr > 0 ? dx / rr : 1.0,
+                                                    rr > 0 ? dy / rr : 0.0};
+    }
+    for (size_t g = 0; g < nfg; ++g) {
+        ctx->geoms[g0 + g].pair0 = base + off[g];
+        ctx->geoms[g0 + g].pair1 = base + off[g + 1];
+    }
+    // tables, in parallel over geometries
+    ctx->free_tables.assign(nfg * NTAB * (size_t)P * P, cd{0, 0});
+    const int nth = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    std::vector<std::thread> pool;
+    for (int w = 0; w < nth; ++w)
+        pool.emplace_back([&, w]() {
+            for (size_t g = w; g < nfg; g += nth) {
+                const Geom &G = ctx->geoms[g0 + g];
+                const CompDev &c = ctx->comps[G.comp];
+                free_m2l_tables(p, zc(ctx->med.k[c.l].x, ctx->med.k[c.l].y), G.rho, G.zs - G.zt,
+                                &ctx->free_tables[g * NTAB * (size_t)P * P], nullptr);
+            }
+        });
+    for (auto &t : pool) t.join();
+    return LMFMM_OK;
 }
 
 }  // namespace lmf

@@ -87,11 +87,17 @@ struct lmfmm_ctx {
     double root_c[3]{}, root_h = 0;
     std::vector<lmf::Box> boxes;
     std::vector<std::vector<int64_t>> lvl0, lvl1;   // [layer][level] box ranges
-    // components
+    // components: the reaction components (l, l', *, star) first, then (free-space
+    // part requested) one free-space pseudo-component per layer with points
     std::vector<CompDev> comps;
-    // far field
+    int n_react_comps = 0;
+    // far field: reaction geometries first, then the free-space ones
     std::vector<lmf::Geom> geoms;
+    size_t n_react_geoms = 0;
     std::vector<lmf::M2LPair> m2l;                  // grouped by geometry
+    std::vector<cd> free_tables;                    // [free geometry][5][P][P], unscaled
+    std::vector<std::pair<int64_t, int64_t>> free_near;   // (source leaf, target leaf), same layer
+    int64_t n_free_pp = 0;
     std::vector<lmf::NearPair> near;
     int64_t n_near_pp = 0;
     std::vector<lmf::TransGroup> tgroups;
@@ -134,6 +140,15 @@ inline double medium_a(const MediumDev &M)
 
 // host_setup.cpp
 lmfmm_status build_host_structures(lmfmm_ctx *ctx);
+// Free-space part: same-layer dual traversal into far and near pairs, free
+// geometries appended to ctx->geoms / ctx->m2l, their tables into free_tables.
+lmfmm_status build_free_structures(lmfmm_ctx *ctx);
+// The five tables (kernel convention of the reaction M2L, phases factored out)
+// of the free-space M2L between two boxes with c_s - c_t = (rho, 0, dz): the
+// singular-to-regular translation composed with (I + grad grad / k^2), times
+// ik / (4 pi) (eqs. freespace3dmulexpscaled, maxwell_M2L_freespace); out5
+// [5][P][P]; blocks9 (optional) [3 out][3 in][P][P] the full helical operator.
+void free_m2l_tables(int p, zc k, double rho, double dz, cd *out5, cd *blocks9);
 // Every (component, source leaf, target leaf) pair of the context as a near
 // pair (the all-pairs direct evaluation), written to out[0 .. cap); returns the
 // number of pairs, or -1 if there are more than cap (nothing past cap is

@@ -65,6 +65,61 @@ void launch_scatter_out(int64_t N, const int64_t *perm, const cd *phih, void *Ph
         k_scatter_out<cd><<<g, 256, 0, st>>>(N, perm, phih, (cd *)Phi, conj_out);
 }
 
+// Transposes of the two helical maps, for the transposed operator
+// A^T = G^T H^T S^T of A = S H G (G: gather_in, S: scatter_out, H: the helical
+// operator).  G = [[1, i, 0], [1, -i, 0], [0, 0, 1]] and
+// S = [[1/2, 1/2, 0], [-i/2, i/2, 0], [0, 0, 1]] act on (x, y, z) and (A, B, C).
+// ph_bar[i] = S^T y[perm[i]] (optionally of conj y)
+template <typename TI>
+__global__ void k_gather_tr(int64_t N, const int64_t *perm, const TI *y, cd *phb, int cj)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    int64_t o = perm[i];
+    cd x = load_c(y + 3 * o), yy = load_c(y + 3 * o + 1), z = load_c(y + 3 * o + 2);
+    if (cj) { x = conj(x); yy = conj(yy); z = conj(z); }
+    phb[3 * i] = 0.5 * (x - mul_i(yy));
+    phb[3 * i + 1] = 0.5 * (x + mul_i(yy));
+    phb[3 * i + 2] = z;
+}
+
+// out[perm[i]] = G^T qh_bar[i] (optionally conjugated)
+template <typename TO>
+__global__ void k_scatter_tr(int64_t N, const int64_t *perm, const cd *qhb, TO *out, int cj)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    int64_t o = perm[i];
+    const cd a = qhb[3 * i], b = qhb[3 * i + 1];
+    cd x = a + b, y = mul_i(a - b), z = qhb[3 * i + 2];
+    if (cj) { x = conj(x); y = conj(y); z = conj(z); }
+    using E = decltype(out->x);
+    out[3 * o] = TO{(E)x.x, (E)x.y};
+    out[3 * o + 1] = TO{(E)y.x, (E)y.y};
+    out[3 * o + 2] = TO{(E)z.x, (E)z.y};
+}
+
+void launch_gather_tr(int64_t N, const int64_t *perm, const void *y, int dtype, cd *phb, bool conj_in,
+                      cudaStream_t st)
+{
+    if (N <= 0) return;
+    const unsigned g = (unsigned)((N + 255) / 256);
+    if (dtype == LMFMM_C64)
+        k_gather_tr<cf><<<g, 256, 0, st>>>(N, perm, (const cf *)y, phb, conj_in);
+    else
+        k_gather_tr<cd><<<g, 256, 0, st>>>(N, perm, (const cd *)y, phb, conj_in);
+}
+void launch_scatter_tr(int64_t N, const int64_t *perm, const cd *qhb, void *out, int dtype, bool conj_out,
+                       cudaStream_t st)
+{
+    if (N <= 0) return;
+    const unsigned g = (unsigned)((N + 255) / 256);
+    if (dtype == LMFMM_C64)
+        k_scatter_tr<cf><<<g, 256, 0, st>>>(N, perm, qhb, (cf *)out, conj_out);
+    else
+        k_scatter_tr<cd><<<g, 256, 0, st>>>(N, perm, qhb, (cd *)out, conj_out);
+}
+
 // --------------------------------------------------------------- P2M, L2P
 // ------------------------------------------------- basis of a chunk of points
 // b_nm(r) = scale * j_n(k |r|) Y_n^m(r^) / s^n with Y_n^m = P^_n^|m| e^{i m phi}
@@ -287,11 +342,13 @@ constexpr size_t LEAF_SMEM_CAP = 200 * 1024;   // dynamic shared memory granted 
 
 // One CTA per leaf: chunks of CH points are turned into their basis by the
 // whole CTA, then each thread accumulates its multipole coefficients over the
-// chunk's points.
+// chunk's points.  The basis is P2M's (conj_basis, scale = 4 pi: eq. mecoeff)
+// or L2P's (plain Y, scale 1), the latter for the transpose of L2P, whose
+// coefficients sum the point values against the same functions L2P evaluates.
 template <typename T>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_p2m(int p, int CH, const int64_t *leaves, const BoxDev *boxes,
                                              const double *xyz, const cd *qh, MediumDev M, LayerScale ls,
-                                             cx<T> *me)
+                                             cx<T> *me, int conj_basis, double scale)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int P = (p + 1) * (p + 1);
@@ -315,7 +372,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_p2m(int p, int 
         const int np = (int)min((int64_t)CH, b.p1 - c0);
         for (int e = threadIdx.x; e < 3 * np; e += blockDim.x)
             hq[e] = cx<T>{(T)qh[3 * c0 + e].x, (T)qh[3 * c0 + e].y};
-        chunk_basis<T>(p, k, xyz, b.c, c0, np, true, 4.0 * LMF_PI, inv_s, L, jr, geo, kz, bas);
+        chunk_basis<T>(p, k, xyz, b.c, c0, np, conj_basis != 0, scale, inv_s, L, jr, geo, kz, bas);
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < PERMAX; ++i) {
@@ -338,11 +395,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_p2m(int p, int 
 
 // One CTA per leaf: chunks of CH target points are turned into their basis by
 // the whole CTA, then one warp per point contracts it with the three local
-// expansions held in shared memory.
+// expansions held in shared memory.  The basis is L2P's (plain Y, scale 1:
+// eq. maxwell_LE_layered) or P2M's (conj_basis, scale 4 pi), the latter for the
+// transpose of P2M.  accumulate: add into ph instead of overwriting it.
 template <typename T>
 __global__ void __launch_bounds__(256) k_l2p(int p, int CH, const int64_t *leaves, const BoxDev *boxes,
                                              const double *xyz, const cx<T> *le, MediumDev M, LayerScale ls,
-                                             cd *ph)
+                                             cd *ph, int conj_basis, double scale, int accumulate)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int P = (p + 1) * (p + 1);
@@ -361,7 +420,7 @@ __global__ void __launch_bounds__(256) k_l2p(int p, int CH, const int64_t *leave
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
     for (int64_t c0 = b.p0; c0 < b.p1; c0 += CH) {
         const int np = (int)min((int64_t)CH, b.p1 - c0);
-        chunk_basis<T>(p, k, xyz, b.c, c0, np, false, 1.0, inv_s, L, jr, geo, kz, bas);
+        chunk_basis<T>(p, k, xyz, b.c, c0, np, conj_basis != 0, scale, inv_s, L, jr, geo, kz, bas);
         __syncthreads();
         for (int j = warp; j < np; j += nwarp) {
             cx<T> A{T(0), T(0)}, B{T(0), T(0)}, C{T(0), T(0)};
@@ -382,9 +441,12 @@ __global__ void __launch_bounds__(256) k_l2p(int p, int CH, const int64_t *leave
             }
             if (lane == 0) {
                 const int64_t t = c0 + j;
-                ph[3 * t] = cd{(double)A.x, (double)A.y};
-                ph[3 * t + 1] = cd{(double)B.x, (double)B.y};
-                ph[3 * t + 2] = cd{(double)C.x, (double)C.y};
+                cd o[3] = {cd{(double)A.x, (double)A.y}, cd{(double)B.x, (double)B.y}, cd{(double)C.x, (double)C.y}};
+                if (accumulate)
+                    for (int v = 0; v < 3; ++v) o[v] += ph[3 * t + v];
+                ph[3 * t] = o[0];
+                ph[3 * t + 1] = o[1];
+                ph[3 * t + 2] = o[2];
             }
         }
         __syncthreads();
@@ -394,35 +456,37 @@ __global__ void __launch_bounds__(256) k_l2p(int p, int CH, const int64_t *leave
 template <typename T>
 void launch_p2m(int p, int64_t nleaf, const int64_t *leaves, const BoxDev *boxes,
                 const double *xyz, const cd *qh, const MediumDev &M, const LayerScale &ls,
-                cx<T> *me, cudaStream_t st)
+                cx<T> *me, cudaStream_t st, bool l2p_basis)
 {
     if (nleaf <= 0) return;
     const LeafSmem<T> sp = leaf_smem<T>(p, false, LEAF_SMEM_CAP);
-    k_p2m<T><<<(unsigned)nleaf, 256, sp.total, st>>>(p, sp.CH, leaves, boxes, xyz, qh, M, ls, me);
+    k_p2m<T><<<(unsigned)nleaf, 256, sp.total, st>>>(p, sp.CH, leaves, boxes, xyz, qh, M, ls, me, l2p_basis ? 0 : 1,
+                                                     l2p_basis ? 1.0 : 4.0 * LMF_PI);
 }
 
 template <typename T>
 void launch_l2p(int p, int64_t nleaf, const int64_t *leaves, const BoxDev *boxes,
                 const double *xyz, const cx<T> *le, const MediumDev &M, const LayerScale &ls,
-                cd *phih, cudaStream_t st)
+                cd *phih, cudaStream_t st, bool p2m_basis, bool accumulate)
 {
     if (nleaf <= 0) return;
     const LeafSmem<T> sp = leaf_smem<T>(p, true, LEAF_SMEM_CAP);
-    k_l2p<T><<<(unsigned)nleaf, 256, sp.total, st>>>(p, sp.CH, leaves, boxes, xyz, le, M, ls, phih);
+    k_l2p<T><<<(unsigned)nleaf, 256, sp.total, st>>>(p, sp.CH, leaves, boxes, xyz, le, M, ls, phih, p2m_basis ? 1 : 0,
+                                                     p2m_basis ? 4.0 * LMF_PI : 1.0, accumulate ? 1 : 0);
 }
 
 template void launch_p2m<float>(int, int64_t, const int64_t *, const BoxDev *, const double *,
                                 const cd *, const MediumDev &, const LayerScale &, cf *,
-                                cudaStream_t);
+                                cudaStream_t, bool);
 template void launch_p2m<double>(int, int64_t, const int64_t *, const BoxDev *, const double *,
                                  const cd *, const MediumDev &, const LayerScale &, cd *,
-                                 cudaStream_t);
+                                 cudaStream_t, bool);
 template void launch_l2p<float>(int, int64_t, const int64_t *, const BoxDev *, const double *,
                                 const cf *, const MediumDev &, const LayerScale &, cd *,
-                                cudaStream_t);
+                                cudaStream_t, bool, bool);
 template void launch_l2p<double>(int, int64_t, const int64_t *, const BoxDev *, const double *,
                                  const cd *, const MediumDev &, const LayerScale &, cd *,
-                                 cudaStream_t);
+                                 cudaStream_t, bool, bool);
 
 // --------------------------------------------------------------------- S2T
 // For every point pair (j in the source leaf, i in the target leaf) of a near
@@ -652,6 +716,132 @@ __global__ void __launch_bounds__(256) k_s2t_apply8(int64_t nrow, const S2TRow *
     atomicAdd(&ph[3 * ti + 1].y, Bv.y);
     atomicAdd(&ph[3 * ti + 2].x, Cv.x);
     atomicAdd(&ph[3 * ti + 2].y, Cv.y);
+}
+
+// Transpose of k_s2t_apply8: qh_bar(j) += K(i, j)^T ph_bar(i) over the targets i
+// of each near pair, K the 3 x 3 helical block of the pair (i, j) with rows
+// (A, B, C) = [[k0, k6, k2], [k7, k0, k3], [k5, k4, k1]] in (a, b, c).  One
+// warp per (near pair, source j): lanes take the targets (coalesced reads of
+// the coefficient rows), a shuffle reduction sums them.
+__global__ void __launch_bounds__(256) k_s2t_apply8_tr(int64_t nrow, const S2TRowT *rows, const NearPair *near,
+                                                       const BoxDev *boxes, const cd *coef8, const cd *phb,
+                                                       cd *qhb)
+{
+    const int64_t wi = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wi >= nrow) return;
+    const S2TRowT w = rows[wi];
+    const NearPair np = near[w.pair];
+    const BoxDev B = boxes[np.src], C = boxes[np.tgt];
+    const int64_t nC = C.p1 - C.p0;
+    const cd *K = coef8 + np.coef0 * 8 + (int64_t)w.jj * 8 * nC;
+    cd a = mkd(0.0), b = mkd(0.0), c = mkd(0.0);
+    for (int64_t ii = lane; ii < nC; ii += 32) {
+        const cd *pi = phb + 3 * (C.p0 + ii);
+        const cd A = pi[0], Bv = pi[1], Cv = pi[2];
+        const cd k0 = K[ii], k1 = K[nC + ii], k2 = K[2 * nC + ii], k3 = K[3 * nC + ii], k4 = K[4 * nC + ii],
+                 k5 = K[5 * nC + ii], k6 = K[6 * nC + ii], k7 = K[7 * nC + ii];
+        a += k0 * A + k7 * Bv + k5 * Cv;
+        b += k6 * A + k0 * Bv + k4 * Cv;
+        c += k2 * A + k3 * Bv + k1 * Cv;
+    }
+    double v[6] = {a.x, a.y, b.x, b.y, c.x, c.y};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int u = 0; u < 6; ++u) v[u] += __shfl_xor_sync(0xffffffffu, v[u], o);
+    if (lane == 0) {
+        double *q = (double *)(qhb + 3 * (B.p0 + w.jj));
+#pragma unroll
+        for (int u = 0; u < 6; ++u) atomicAdd(q + u, v[u]);
+    }
+}
+
+void launch_s2t_apply8_tr(int64_t nrow, const S2TRowT *rows, const NearPair *near, const BoxDev *boxes,
+                          const cd *coef8, const cd *phb, cd *qhb, cudaStream_t st)
+{
+    if (nrow <= 0) return;
+    k_s2t_apply8_tr<<<(unsigned)((nrow * 32 + 255) / 256), 256, 0, st>>>(nrow, rows, near, boxes, coef8, phb, qhb);
+}
+
+// Free-space near field (Section 2, eq. GEandGH): ph(i) += T G_E^f(r_i - r_j)
+// T^{-1} qh(j) over the sources j != i of the near leaf pairs of the target's
+// layer, G_E^f = g (a I + b R^ R^T), g = e^{ikR} / (4 pi R),
+// a = 1 + (ik/R - 1/R^2)/k^2, b = (3/R^2 - 3ik/R - k^2)/k^2, T the helical map
+// (A, B, C) = (x + iy, x - iy, z).  One warp per (near pair, row point): lanes
+// take the column points, a shuffle reduction sums them.  transposed: rows are
+// the pair's sources and the maps are T^T in, T^{-T} out (G_E^f is symmetric
+// and even in R), which is the transpose of the forward sum.
+__global__ void __launch_bounds__(256) k_p2p_free(int64_t nrow, const S2TRowT *rows, const int64_t *pairs,
+                                                  const BoxDev *boxes, const double *xyz, MediumDev M,
+                                                  const cd *in, cd *out, int transposed)
+{
+    const int64_t wi = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wi >= nrow) return;
+    const S2TRowT w = rows[wi];
+    const BoxDev Bs = boxes[pairs[2 * w.pair]], Bt = boxes[pairs[2 * w.pair + 1]];
+    // forward: row = target (in Bt), columns = sources (Bs); transposed: the reverse
+    const BoxDev Br = transposed ? Bs : Bt, Bc = transposed ? Bt : Bs;
+    const int64_t ir = Br.p0 + w.jj;
+    const cd k = M.k[Br.layer];
+    const cd ik2 = inv(k * k);
+    const double xr = xyz[3 * ir], yr = xyz[3 * ir + 1], zr = xyz[3 * ir + 2];
+    cd vx = mkd(0.0), vy = mkd(0.0), vz = mkd(0.0);
+    for (int64_t jc = Bc.p0 + lane; jc < Bc.p1; jc += 32) {
+        if (jc == ir) continue;
+        const double Rx = xr - xyz[3 * jc], Ry = yr - xyz[3 * jc + 1], Rz = zr - xyz[3 * jc + 2];
+        const double R2 = Rx * Rx + Ry * Ry + Rz * Rz, R = sqrt(R2), iR = 1.0 / R;
+        const cd g = (0.25 / LMF_PI * iR) * cexpd(mul_i(R * k));
+        const cd ikR = mul_i(k * iR);
+        const cd a = mkd(1.0) + ik2 * (ikR - mkd(iR * iR));
+        const cd b = ik2 * (mkd(3.0 * iR * iR) - 3.0 * ikR - k * k);
+        const cd *q = in + 3 * jc;
+        cd jx, jy, jz;   // Cartesian input
+        if (!transposed) {
+            jx = 0.5 * (q[0] + q[1]);
+            jy = mul_mi(0.5 * (q[0] - q[1]));
+        } else {
+            jx = q[0] + q[1];
+            jy = mul_i(q[0] - q[1]);
+        }
+        jz = q[2];
+        const cd rj = (iR * iR) * (Rx * jx + Ry * jy + Rz * jz);
+        vx += g * (a * jx + b * (Rx * rj));
+        vy += g * (a * jy + b * (Ry * rj));
+        vz += g * (a * jz + b * (Rz * rj));
+    }
+    double v[6] = {vx.x, vx.y, vy.x, vy.y, vz.x, vz.y};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int u = 0; u < 6; ++u) v[u] += __shfl_xor_sync(0xffffffffu, v[u], o);
+    if (lane == 0) {
+        const cd X{v[0], v[1]}, Y{v[2], v[3]};
+        cd o0, o1;
+        if (!transposed) {
+            o0 = X + mul_i(Y);
+            o1 = X - mul_i(Y);
+        } else {
+            o0 = 0.5 * (X - mul_i(Y));
+            o1 = 0.5 * (X + mul_i(Y));
+        }
+        double *op = (double *)(out + 3 * ir);
+        atomicAdd(op, o0.x);
+        atomicAdd(op + 1, o0.y);
+        atomicAdd(op + 2, o1.x);
+        atomicAdd(op + 3, o1.y);
+        atomicAdd(op + 4, v[4]);
+        atomicAdd(op + 5, v[5]);
+    }
+}
+
+void launch_p2p_free(int64_t nrow, const S2TRowT *rows, const int64_t *pairs, const BoxDev *boxes,
+                     const double *xyz, const MediumDev &M, const cd *in, cd *out, bool transposed, cudaStream_t st)
+{
+    if (nrow <= 0) return;
+    k_p2p_free<<<(unsigned)((nrow * 32 + 255) / 256), 256, 0, st>>>(nrow, rows, pairs, boxes, xyz, M, in, out,
+                                                                     transposed ? 1 : 0);
 }
 
 void launch_s2t_combine(int64_t nnear, const NearPair *near, const BoxDev *boxes, const double *xyz,

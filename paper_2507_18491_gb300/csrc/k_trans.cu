@@ -52,7 +52,9 @@ __device__ __forceinline__ void lds_vec(const cx<T> *src, cx<T> (&dst)[N])
     }
 }
 
-template <typename T, typename Store>
+// TRA: multiply by A^T (A read column-wise: consecutive threads take
+// consecutive rows of A^T, i.e. consecutive entries of a row of A)
+template <typename T, typename Store, bool TRA = false>
 __device__ __forceinline__ void tiled_gemm(int P, int r_tile, const cx<T> *__restrict__ A, const cx<T> *X,
                                            cx<T> *As, int ncol, Store store)
 {
@@ -60,18 +62,25 @@ __device__ __forceinline__ void tiled_gemm(int P, int r_tile, const cx<T> *__res
     constexpr int TM = G::TM, TN = G::TN, BK = G::BK, BM = G::BM, BMP = G::BMP;
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     const int nk = (P + BK - 1) / BK;
+    auto rk = [](int e, int &r, int &kk) {
+        if (TRA) { r = e % BM; kk = e / BM; }
+        else { r = e / BK; kk = e % BK; }
+    };
     auto fetch = [&](int r0, int k0, cx<T> (&v)[G::LPT]) {
 #pragma unroll
         for (int u = 0; u < G::LPT; ++u) {
-            const int e = threadIdx.x + 256 * u, r = e / BK, kk = e % BK;
+            int r, kk;
+            rk(threadIdx.x + 256 * u, r, kk);
             const int gr = r0 + r, gk = k0 + kk;
-            v[u] = (gr < P && gk < P) ? A[(int64_t)gr * P + gk] : cx<T>{T(0), T(0)};
+            v[u] = (gr < P && gk < P) ? (TRA ? A[(int64_t)gk * P + gr] : A[(int64_t)gr * P + gk])
+                                      : cx<T>{T(0), T(0)};
         }
     };
     auto put = [&](int buf, const cx<T> (&v)[G::LPT]) {
 #pragma unroll
         for (int u = 0; u < G::LPT; ++u) {
-            const int e = threadIdx.x + 256 * u, r = e / BK, kk = e % BK;
+            int r, kk;
+            rk(threadIdx.x + 256 * u, r, kk);
             As[buf * BK * BMP + kk * BMP + r] = v[u];
         }
     };
@@ -254,6 +263,85 @@ __global__ void __launch_bounds__(256) k_m2l(int p, const M2LWork *work, const G
     });
 }
 
+// Transpose of k_m2l: the forward map of a column is
+//   le[tgt][vout][out(r)] += F_out(r) sum_k A[r][k] F_in(k) me[src][vin][in(k)]
+// (F_in, F_out, in(k), out(r) the factors and the kappa < 0 order flips above),
+// so its transpose gathers F_out(r) le_bar[tgt][vout][out(r)] into the rows r,
+// multiplies by A^T and scatters F_in(k) (A^T x)_k into me_bar[src][vin][in(k)].
+template <typename T>
+__global__ void __launch_bounds__(256) k_m2l_tr(int p, const M2LWork *work, const GeomDev *geoms,
+                                                const CompDev *comps, const M2LPair *pairs,
+                                                const cx<T> *tab, const cx<T> *le_bar, cx<T> *me_bar)
+{
+    constexpr int BN = 16 * TileCfg<T>::TN;
+    extern __shared__ unsigned char smraw[];
+    const int P = (p + 1) * (p + 1);
+    const int MW = 2 * p + 5;
+    cx<T> *X = (cx<T> *)smraw;
+    cx<T> *As = X + (size_t)P * GemmTile<T>::BNP;
+    cx<T> *E = As + 2 * GemmTile<T>::BK * GemmTile<T>::BMP;
+    short *NN = (short *)(E + BN * MW);
+    M2LWork w = work[blockIdx.x];
+    const GeomDev &g = geoms[w.geom];
+    const CompDev c = comps[g.comp];
+    const int t = w.t;
+    const int ncpp = (t == 1) ? 1 : 2;
+    const int ncol = w.npair * ncpp;
+    const bool sneg = c.s < 0;
+    for (int pp = threadIdx.x; pp < w.npair; pp += blockDim.x) {
+        M2LPair pr = pairs[w.pair0 + pp];
+        cd b = {pr.cphi, pr.sphi}, e = mkd(1.0);
+        cx<T> *row = E + pp * MW + (p + 2);
+        row[0] = cx<T>{T(1), T(0)};
+        for (int m = 1; m <= p + 2; ++m) {
+            e = e * b;
+            row[m] = cx<T>{(T)e.x, (T)e.y};
+            row[-m] = cx<T>{(T)e.x, (T)(-e.y)};
+        }
+    }
+    for (int k = threadIdx.x; k < P; k += blockDim.x) {
+        int n = (int)sqrtf((float)k + 0.5f);
+        while ((n + 1) * (n + 1) <= k) ++n;
+        while (n * n > k) --n;
+        NN[k] = (short)n;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < P * BN; e += blockDim.x) {
+        int r = e / BN, col = e % BN;
+        cx<T> v{T(0), T(0)};
+        if (col < ncol) {
+            int pp = col / ncpp, j = col % ncpp;
+            ColSpec cs = c_cols[t][j];
+            int nu = NN[r], mh = r - nu * nu - nu;
+            int mu = cs.kap < 0 ? -mh : mh;
+            int e2 = nu + mu;
+            cx<T> sc = ipow<T>(-e2);
+            if ((sneg && (e2 & 1)) != (c.has_tgt_refl && (e2 & 1))) sc = -sc;
+            T cf = (T)cs.coef;
+            if (cs.kap < 0 && (cs.kap & 1)) cf = -cf;
+            cx<T> k1 = ipow<T>(1 + cs.kap);
+            cx<T> ph = E[pp * MW + (p + 2) + cs.kap - mu];
+            cx<T> x = le_bar[(pairs[w.pair0 + pp].tgt * 3 + cs.vout) * P + nu * nu + nu + mu];
+            v = (cf * sc) * (k1 * (ph * x));
+        }
+        X[r * GemmTile<T>::BNP + col] = v;
+    }
+    __syncthreads();
+    const cx<T> *A = tab + ((int64_t)g.tab_index * NTAB + t) * P * P;
+    auto store = [&](int k, int col, cx<T> y) {
+        int pp = col / ncpp, j = col % ncpp;
+        ColSpec cs = c_cols[t][j];
+        int n = NN[k], m = k - n * n - n;
+        int ms = cs.kap < 0 ? -m : m;
+        int e1 = n + ms;
+        cx<T> sc = ipow<T>(e1);
+        if ((sneg && (e1 & 1)) != (c.has_src_refl && (e1 & 1))) sc = -sc;
+        cx<T> yy = sc * (E[pp * MW + (p + 2) + ms] * y);
+        atomic_add_cx(me_bar + (pairs[w.pair0 + pp].src * 3 + cs.vin) * P + n * n + n + ms, yy);
+    };
+    tiled_gemm<T, decltype(store), true>(P, blockIdx.y, A, X, As, ncol, store);
+}
+
 // tab_T[g][t][nu mu][n' m'] = I-hat * s_t^nu * s_s^n'  (level scaling, cast to T)
 template <typename T>
 __global__ void k_scale_tables(int p, int64_t g0, int64_t ng, const GeomDev *geoms,
@@ -327,6 +415,17 @@ void launch_m2l_t(int p, int64_t nwork, const M2LWork *work, const GeomDev *geom
 }
 
 template <typename T>
+void launch_m2l_tr(int p, int64_t nwork, const M2LWork *work, const GeomDev *geoms,
+                   const CompDev *comps, const M2LPair *pairs, const cx<T> *tab, const cx<T> *le_bar,
+                   cx<T> *me_bar, cudaStream_t st)
+{
+    if (nwork <= 0) return;
+    const unsigned nrt = (unsigned)(((p + 1) * (p + 1) + GemmTile<T>::BM - 1) / GemmTile<T>::BM);
+    k_m2l_tr<T><<<dim3((unsigned)nwork, nrt), 256, gemm_smem<T>(p), st>>>(p, work, geoms, comps, pairs, tab,
+                                                                           le_bar, me_bar);
+}
+
+template <typename T>
 void launch_scale_tables(int p, int64_t g0, int64_t ng, const GeomDev *geoms, const cd *tab64,
                          cx<T> *tab, cudaStream_t st)
 {
@@ -347,6 +446,10 @@ template void launch_m2l_t<float>(int, int64_t, const M2LWork *, const GeomDev *
 template void launch_m2l_t<double>(int, int64_t, const M2LWork *, const GeomDev *,
                                    const CompDev *, const M2LPair *, const cd *, const cd *, cd *,
                                    cudaStream_t);
+template void launch_m2l_tr<float>(int, int64_t, const M2LWork *, const GeomDev *, const CompDev *,
+                                   const M2LPair *, const cf *, const cf *, cf *, cudaStream_t);
+template void launch_m2l_tr<double>(int, int64_t, const M2LWork *, const GeomDev *, const CompDev *,
+                                    const M2LPair *, const cd *, const cd *, cd *, cudaStream_t);
 template void launch_scale_tables<float>(int, int64_t, int64_t, const GeomDev *, const cd *, cf *,
                                          cudaStream_t);
 template void launch_scale_tables<double>(int, int64_t, int64_t, const GeomDev *, const cd *,
@@ -360,6 +463,8 @@ cudaError_t configure_trans_kernels()
     if ((e = cudaFuncSetAttribute(k_group_gemm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_m2l<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     if ((e = cudaFuncSetAttribute(k_m2l<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_m2l_tr<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+    if ((e = cudaFuncSetAttribute(k_m2l_tr<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
     // these CTAs hold ~100 KB of shared memory: take the whole carveout so that two fit on an SM
     const int mx = (int)cudaSharedmemCarveoutMaxShared;
     if ((e = cudaFuncSetAttribute(k_group_gemm<float>, cudaFuncAttributePreferredSharedMemoryCarveout, mx))) return e;

@@ -74,14 +74,18 @@ void launch_gather_in(int64_t N, const int64_t *perm, const void *J, int dtype, 
                       cudaStream_t st);
 void launch_scatter_out(int64_t N, const int64_t *perm, const cd *phih, void *Phi, int dtype, bool conj_out,
                         cudaStream_t st);
+// P2M of the helical charges qh into me at the leaves; with l2p_basis the
+// coefficients are taken against L2P's functions instead (transpose of L2P)
 template <typename T>
 void launch_p2m(int p, int64_t nleaf, const int64_t *leaves, const BoxDev *boxes,
                 const double *xyz, const cd *qh, const MediumDev &M, const LayerScale &ls,
-                cx<T> *me, cudaStream_t st);
+                cx<T> *me, cudaStream_t st, bool l2p_basis = false);
+// L2P of le at the leaf points into phih; with p2m_basis the expansions are
+// evaluated with P2M's functions (transpose of P2M); accumulate adds into phih
 template <typename T>
 void launch_l2p(int p, int64_t nleaf, const int64_t *leaves, const BoxDev *boxes,
                 const double *xyz, const cx<T> *le, const MediumDev &M, const LayerScale &ls,
-                cd *phih, cudaStream_t st);
+                cd *phih, cudaStream_t st, bool p2m_basis = false, bool accumulate = false);
 
 // k_trans.cu
 cudaError_t configure_trans_kernels();
@@ -94,6 +98,11 @@ template <typename T>
 void launch_m2l_t(int p, int64_t nwork, const M2LWork *work, const GeomDev *geoms,
                   const CompDev *comps, const M2LPair *pairs, const cx<T> *tab, const cx<T> *me,
                   cx<T> *le, cudaStream_t st);
+// transpose of the SIMT M2L: me_bar[src] += (M2L)^T le_bar[tgt], same work items
+template <typename T>
+void launch_m2l_tr(int p, int64_t nwork, const M2LWork *work, const GeomDev *geoms,
+                   const CompDev *comps, const M2LPair *pairs, const cx<T> *tab, const cx<T> *le_bar,
+                   cx<T> *me_bar, cudaStream_t st);
 // k_m2l_tc.cu: mixed-form M2L on tcgen05 tensor cores (3xTF32), p <= 15;
 // status gets bit 4 if a tensor-core wait gave up
 bool m2l_tc_supported(int p);
@@ -103,26 +112,30 @@ cudaError_t launch_m2l_tc(int p, int64_t nwork, const M2LWork *work, const GeomD
                           const CompDev *comps, const M2LPair *pairs, const cf *tab, const cf *me,
                           cf *le, int *status, cudaStream_t st);
 // persistent warp-specialised variant (p <= 12) on a pre-tiled image of the
-// tables in three bf16 pieces (launch_tile_tables from the FP64 tables);
-// ephase holds e^{i d phi} of every pair, d = -(p+2)..p+2 ([npair][2p+5],
-// FP32 from FP64); yscr holds m2l_tc2_scratch_floats(p, nsm) floats, nsm =
-// CTAs of the launch (the SM count)
+// tables in two fp16 pieces with power-of-two row and column scales
+// (launch_tile_tables from the FP64 tables; scales holds
+// m2l_tc2_scale_floats(p, ngeom * 5) floats); ephase holds e^{i d phi} of
+// every pair, d = -(p+2)..p+2 ([npair][2p+5], FP32 from FP64); yscr holds
+// m2l_tc2_scratch_floats(p, nsm) floats, nsm = CTAs of the launch (the SM count)
 bool m2l_tc2_supported(int p);
 size_t m2l_tc2_image_bytes(int p, int64_t ngeom);
 size_t m2l_tc2_scratch_floats(int p, int nsm);
+size_t m2l_tc2_scale_floats(int p, int64_t nmat);
 void launch_tile_tables(int p, int64_t g0, int64_t ng, const GeomDev *geoms, const CompDev *comps,
-                        const cd *tab64, void *img, cudaStream_t st);
+                        const cd *tab64, void *img, float *scales, cudaStream_t st);
 cudaError_t launch_m2l_tc2(int p, int64_t nwork, const M2LWork *work, const GeomDev *geoms,
-                           const M2LPair *pairs, const cf *ephase, const void *img,
+                           const M2LPair *pairs, const cf *ephase, const void *img, const float *scales,
                            const cf *me, cf *le, float *yscr, int nsm, int *status, cudaStream_t st);
 // M2M or L2L on the same kernel: items M2LWork{geom = translation group, t = 0,
 // npair, pair0} over pairs (tsrc[q], tdst[q]), 3 helical columns each; img holds
-// one tiled matrix per group (tile_matrix_tc2, tc2_matrix_bytes(p) each)
+// one tiled matrix per group (tile_matrix_tc2, tc2_matrix_bytes(p) each) and
+// scales its row / column scales (m2l_tc2_scale_floats(p, 1) each)
 cudaError_t launch_trans_tc2(int p, int64_t nwork, const M2LWork *work, const int64_t *tsrc,
-                             const int64_t *tdst, const void *img, const cf *in, cf *out, float *yscr, int nsm,
-                             int *status, cudaStream_t st);
+                             const int64_t *tdst, const void *img, const float *scales, const cf *in, cf *out,
+                             float *yscr, int nsm, int *status, cudaStream_t st);
 size_t tc2_matrix_bytes(int p);
-void tile_matrix_tc2(int p, const cd *M, void *img);   // host: P x P row-major (row = output index)
+// host: P x P row-major (row = output index) -> tiled fp16 image and its scales
+void tile_matrix_tc2(int p, const cd *M, void *img, float *scales);
 template <typename T>
 void launch_scale_tables(int p, int64_t g0, int64_t ng, const GeomDev *geoms, const cd *tab64,
                          cx<T> *tab, cudaStream_t st);
@@ -144,8 +157,37 @@ struct S2TRow {
 };
 void launch_s2t_apply8(int64_t nrow, const S2TRow *rows, const NearPair *near, const BoxDev *boxes,
                        const cd *coef8, const cd *qh, cd *phih, cudaStream_t st);
+// transposed near field: one row per (near pair, source jj), all targets
+struct S2TRowT {
+    int64_t pair;
+    int jj, pad;
+};
+void launch_s2t_apply8_tr(int64_t nrow, const S2TRowT *rows, const NearPair *near, const BoxDev *boxes,
+                          const cd *coef8, const cd *phb, cd *qhb, cudaStream_t st);
+// free-space near field over leaf pairs ([2 * pair] = source leaf, [+1] =
+// target leaf); rows {pair, point index within the row box}: targets (forward,
+// out = ph) or sources (transposed, out = qh_bar)
+void launch_p2p_free(int64_t nrow, const S2TRowT *rows, const int64_t *pairs, const BoxDev *boxes,
+                     const double *xyz, const MediumDev &M, const cd *in, cd *out, bool transposed, cudaStream_t st);
+// transposes of the helical maps: ph_bar = S^T y (caller order -> sorted),
+// out = G^T qh_bar (sorted -> caller order), optional conjugation of y / out
+void launch_gather_tr(int64_t N, const int64_t *perm, const void *y, int dtype, cd *phb, bool conj_in,
+                      cudaStream_t st);
+void launch_scatter_tr(int64_t N, const int64_t *perm, const cd *qhb, void *out, int dtype, bool conj_out,
+                       cudaStream_t st);
 void launch_s2t_apply(int64_t nnear, const NearPair *near, const BoxDev *boxes,
                       const double *xyz, const cd *coef, const cd *qh, cd *phih,
                       cudaStream_t st);
+
+// k_grad.cu: position gradient of the FP64 form (see the file's header).
+// grad (caller order, [N][3] real) is accumulated: zero it first.
+void launch_grad_leaf(int p, int64_t N, int64_t nleaf, const int64_t *leaves, const BoxDev *boxes, const double *xyz,
+                      const int64_t *perm, const cd *le, const cd *meb, const cd *qh, const cd *nu, const MediumDev &M,
+                      const LayerScale &ls, double *grad, cudaStream_t st);
+// 20 derivative integrals per near point pair (coef: [pair coef0 + e][20])
+void launch_s2t_pre_grad(int64_t nnear, const NearPair *near, const BoxDev *boxes, const double *xyz,
+                         const MediumDev &M, const CompDev *comps, double a, int node_cap, cd *coef, cudaStream_t st);
+void launch_grad_near(int64_t nnear, const NearPair *near, const BoxDev *boxes, const double *xyz, const int64_t *perm,
+                      const CompDev *comps, const cd *coefg, const cd *qh, const cd *nu, double *grad, cudaStream_t st);
 
 }  // namespace lmf

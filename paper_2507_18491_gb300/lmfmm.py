@@ -20,6 +20,7 @@ OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_STATE, ERR_QUAD, ERR_UNSUPPORTED, ERR_TIMEOU
     0, -1, -2, -3, -4, -5, -6, -7)
 FP64, MIXED = 0, 1
 C128, C64 = 0, 1
+REACTION, FREE, TOTAL = 0, 1, 2
 
 
 class _Complex128(ctypes.Structure):
@@ -30,7 +31,8 @@ class Params(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int), ("depth", ctypes.c_int), ("leaf_cap", ctypes.c_int),
                 ("theta", ctypes.c_double), ("eta", ctypes.c_double),
                 ("quad_tol", ctypes.c_double), ("precision", ctypes.c_int),
-                ("tensor_cores", ctypes.c_int), ("quad_node_cap", ctypes.c_int)]
+                ("tensor_cores", ctypes.c_int), ("quad_node_cap", ctypes.c_int),
+                ("components", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -43,13 +45,15 @@ class Stats(ctypes.Structure):
                 ("ms_stage", ctypes.c_double * 8), ("m2l_columns", ctypes.c_int64),
                 ("m2l_kernel", ctypes.c_int), ("launches", ctypes.c_int),
                 ("n_geometries_same_layer", ctypes.c_int64), ("ms_tabulate", ctypes.c_double),
-                ("tab_flops", ctypes.c_double)]
+                ("tab_flops", ctypes.c_double), ("adjoint_transposed", ctypes.c_int),
+                ("n_free_geometries", ctypes.c_int64), ("n_free_near_point_pairs", ctypes.c_int64)]
 
 
 EXPORTS = ["lmfmm_default_params", "lmfmm_create", "lmfmm_set_layers", "lmfmm_set_points",
            "lmfmm_set_points_device", "lmfmm_build", "lmfmm_matvec", "lmfmm_matvec_host",
-           "lmfmm_matvec_adjoint", "lmfmm_check", "lmfmm_test_set_status", "lmfmm_direct",
+           "lmfmm_matvec_adjoint", "lmfmm_matvec_transpose", "lmfmm_gradient", "lmfmm_check", "lmfmm_test_set_status", "lmfmm_direct",
            "lmfmm_direct_noalloc", "lmfmm_densities", "lmfmm_m2l_table", "lmfmm_translation_matrix",
+           "lmfmm_free_m2l_table",
            "lmfmm_get_stats", "lmfmm_last_error", "lmfmm_destroy"]
 
 
@@ -84,6 +88,8 @@ def load():
         "lmfmm_matvec": [P, P, i, P, P],
         "lmfmm_matvec_host": [P, P, i, P, P],
         "lmfmm_matvec_adjoint": [P, P, i, P, P],
+        "lmfmm_matvec_transpose": [P, P, i, P, P],
+        "lmfmm_gradient": [P, P, P, i, P, P, P],
         "lmfmm_check": [P, P],
         "lmfmm_test_set_status": [P, i],
         "lmfmm_direct": [P, P, P, P],
@@ -91,6 +97,7 @@ def load():
         "lmfmm_densities": [P, i, i, i64, P, P, P],
         "lmfmm_m2l_table": [P, i, i, i, i, d, d, d, P, P],
         "lmfmm_translation_matrix": [i, _Complex128, ctypes.POINTER(d), P, P],
+        "lmfmm_free_m2l_table": [i, _Complex128, d, d, P, P],
         "lmfmm_get_stats": [P, ctypes.POINTER(Stats)],
         "lmfmm_last_error": [P],
         "lmfmm_destroy": [P],
@@ -195,6 +202,25 @@ def matvec_adjoint(ctx, y, Phi, stream=None):
     _check(load().lmfmm_matvec_adjoint(ctx, py, code, pp, _stream(stream)), ctx)
 
 
+def matvec_transpose(ctx, y, out, stream=None):
+    py, code = _field(y)
+    po, _ = _field(out, like=y)
+    _check(load().lmfmm_matvec_transpose(ctx, py, code, po, _stream(stream)), ctx)
+
+
+def gradient(ctx, J, g, gJ=None, gxyz=None, stream=None):
+    """gJ = A^H g and gxyz = Re sum conj(g) dE/dr (FP64 form; see lmfmm_gradient)."""
+    import torch
+    pj, code = _field(J)
+    pg, _ = _field(g, like=J)
+    pgj = _field(gJ, like=J)[0] if gJ is not None else None
+    if gxyz is not None and not (gxyz.is_cuda and gxyz.dtype == torch.float64 and gxyz.is_contiguous()
+                                 and tuple(gxyz.shape) == (J.shape[0], 3)):
+        raise ValueError("gxyz must be a contiguous float64 CUDA tensor [N, 3]")
+    pgx = ctypes.c_void_p(gxyz.data_ptr()) if gxyz is not None else None
+    _check(load().lmfmm_gradient(ctx, pj, pg, code, pgj, pgx, _stream(stream)), ctx)
+
+
 def check(ctx, stream=None):
     """Wait for the stream and raise if a device wait of the matvecs gave up."""
     _check(load().lmfmm_check(ctx, _stream(stream)), ctx)
@@ -248,6 +274,18 @@ def translation_matrix(p, k, t):
     return up, dn
 
 
+def free_m2l_table(p, k, rho, dz, blocks=False):
+    """(tables [5, P, P], blocks [3, 3, P, P] or None) of the free-space M2L for
+    c_s - c_t = (rho, 0, dz).  Host only."""
+    P = (p + 1) ** 2
+    tab = np.zeros((5, P, P), np.complex128)
+    blk = np.zeros((3, 3, P, P), np.complex128) if blocks else None
+    _check(load().lmfmm_free_m2l_table(int(p), _Complex128(float(np.real(k)), float(np.imag(k))),
+                                       float(rho), float(dz), ctypes.c_void_p(tab.ctypes.data),
+                                       ctypes.c_void_p(blk.ctypes.data) if blocks else None))
+    return tab, blk
+
+
 def get_stats(ctx) -> dict:
     s = Stats()
     _check(load().lmfmm_get_stats(ctx, ctypes.byref(s)), ctx)
@@ -276,8 +314,10 @@ class Operator:
     [N,3], the dtype of J); ``check()`` raises if a device wait gave up."""
 
     def __init__(self, d, k, xyz, p=8, depth=-1, leaf_cap=64, theta=0.55, eta=0.1,
-                 precision=FP64, tensor_cores=True, device=0, quad_node_cap=None):
+                 precision=FP64, tensor_cores=True, device=0, quad_node_cap=None,
+                 components=REACTION):
         prm = default_params()
+        prm.components = int(components)
         if quad_node_cap is not None:
             prm.quad_node_cap = int(quad_node_cap)
         prm.p, prm.depth, prm.leaf_cap = int(p), int(depth), int(leaf_cap)
@@ -307,6 +347,22 @@ class Operator:
         matvec_adjoint(self.ctx, y, out, stream)
         return out
 
+    def tmatvec(self, y, out=None, stream=None):
+        """A^T y with the transposed operators (FP64 / SIMT mixed forms)."""
+        import torch
+        if out is None:
+            out = torch.empty_like(y)
+        matvec_transpose(self.ctx, y, out, stream)
+        return out
+
+    def vjp(self, J, g, stream=None):
+        """(A^H g, Re sum conj(g) dE/dr) for E = A(r) J (FP64 form)."""
+        import torch
+        gJ = torch.empty_like(J)
+        gx = torch.empty((J.shape[0], 3), dtype=torch.float64, device=J.device)
+        gradient(self.ctx, J, g, gJ, gx, stream)
+        return gJ, gx
+
     def check(self, stream=None):
         check(self.ctx, stream)
 
@@ -330,3 +386,55 @@ class Operator:
             self.close()
         except Exception:
             pass
+
+
+class ReactionField:
+    """E = A(r) J as a differentiable torch function of the currents J and the
+    point coordinates r (FP64 form).  ``ReactionField(d, k, xyz, **kw)`` builds
+    the operator at the coordinates xyz; ``apply(J, xyz_tensor)`` returns E and,
+    under autograd, backpropagates into J (A^H g) and into the coordinates
+    (Re sum conj(g) dE/dr, tree and lists held fixed) through lmfmm_gradient,
+    which recomputes the forward expansions it needs (checkpointed on the
+    device) instead of keeping them from the forward call."""
+
+    def __init__(self, d, k, xyz, **kw):
+        kw.setdefault("precision", FP64)
+        self.op = Operator(d, k, xyz, **kw).build()
+
+    def apply(self, J, xyz):
+        return _ReactionFieldFn.apply(J, xyz, self.op)
+
+    def close(self):
+        self.op.close()
+
+
+def _make_fn():
+    import torch
+
+    class Fn(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, J, xyz, op):
+            ctx.op = op
+            ctx.save_for_backward(J)
+            return op.matvec(J.contiguous())
+
+        @staticmethod
+        def backward(ctx, g):
+            (J,) = ctx.saved_tensors
+            gJ, gx = ctx.op.vjp(J.contiguous(), g.contiguous())
+            return gJ, gx, None
+
+    return Fn
+
+
+class _LazyFn:
+    _fn = None
+
+    @classmethod
+    def apply(cls, *args):
+        if cls._fn is None:
+            cls._fn = _make_fn()
+        return cls._fn.apply(*args)
+
+
+_ReactionFieldFn = _LazyFn

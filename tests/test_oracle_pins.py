@@ -8,6 +8,7 @@ import pytest
 import scipy.special as sp
 
 import oracle as O
+from paper_2507_18491_gb300 import workloads as W
 
 D3 = [0.0, -1.2]
 K3 = np.array([0.8, 1.5, 2.0]) + 0.01j
@@ -276,3 +277,20 @@ def test_quadrature_tolerance_refinement():
     G1 = O.greact([0.0], np.array([0.8, 1.2]), r, rp, rtol=1e-8)
     G2 = O.greact([0.0], np.array([0.8, 1.2]), r, rp, rtol=1e-12)
     assert rel(G1, G2) < 1e-8
+
+
+def test_direct_free_is_the_sum_of_closed_form_dyads():
+    """The oracle's free-space direct sum is sum_{j != i, same layer} of the
+    closed-form dyad (itself pinned against the Sommerfeld assembly above)."""
+    rng = np.random.default_rng(12)
+    d, k = np.array([0.0, -1.2]), np.array([0.8, 1.5, 2.0]) + 0.01j
+    xyz = W.points_in_layers(rng, d, [5, 4, 6], margin=0.1, xy=0.8)
+    J = W.currents(rng, xyz.shape[0])
+    got = O.direct_free(d, k, xyz, J)
+    lay = [O.layer_of(d, z) for z in xyz[:, 2]]
+    for i in range(xyz.shape[0]):
+        ref = np.zeros(3, complex)
+        for j in range(xyz.shape[0]):
+            if j != i and lay[j] == lay[i]:
+                ref += O.gfree(k[lay[i]], xyz[i], xyz[j]) @ J[j]
+        np.testing.assert_allclose(got[i], ref, rtol=1e-13, atol=1e-13 * np.abs(ref).max())
