@@ -296,6 +296,47 @@ lmfmm_status lmfmm_free_m2l_table(int p, lmfmm_c128 k, double rho, double dz, lm
 
 lmfmm_status lmfmm_get_stats(const lmfmm_ctx *ctx, lmfmm_stats *out);
 
+/* ------------------------------------------------------------- batches
+ * Many layered problems (own media, points, sizes; one device, one p, one
+ * precision) applied together.  lmfmm_batch_matvec records every problem's
+ * upward pass, one merged persistent M2L launch over all problems' work items
+ * (when every problem runs the persistent tensor-core M2L, i.e. the mixed
+ * form with tensor_cores 1 or 3 and p <= 12; otherwise each problem's own
+ * M2L), and every downward pass into a CUDA graph on its first call, and
+ * replays that graph while the caller's pointers stay the same (new
+ * pointers: a new capture).  The contexts stay owned by the caller and must
+ * outlive the batch; a batch must not be used from two host threads at once. */
+typedef struct lmfmm_batch lmfmm_batch;
+
+lmfmm_status lmfmm_batch_create(lmfmm_batch **out, lmfmm_ctx *const *ctxs, int n);
+
+/* Phi[i] = A_i J[i] for every problem i: J, Phi host arrays of n DEVICE
+ * pointers, each [N_i][3] of element type dtype.  Asynchronous on stream (the
+ * graph runs there); device-side failures via lmfmm_batch_check. */
+lmfmm_status lmfmm_batch_matvec(lmfmm_batch *b, const void *const *J, void *const *Phi, int dtype,
+                                void *stream);
+
+/* Autotuner of the merged M2L's work tiles: times the persistent launch
+ * (device events, best of three after a warm run, on zeroed expansions) with
+ * the work items cut to 64 or 32 helical columns (one MMA tile of 128 real
+ * rows, or half of it) and ordered problem by problem or round robin, and
+ * keeps the fastest (lmfmm_batch_info).  Synchronous.  LMFMM_ERR_UNSUPPORTED
+ * when the batch has no merged M2L. */
+lmfmm_status lmfmm_batch_tune(lmfmm_batch *b, void *stream);
+
+/* Waits for stream; LMFMM_ERR_TIMEOUT if a bounded tensor-core wait of the
+ * batch's launches gave up. */
+lmfmm_status lmfmm_batch_check(lmfmm_batch *b, void *stream);
+
+/* merged: 1 if the M2L runs as one launch; nwork: its work items; variant:
+ * the tuned tiling (bit 0 round robin, bit 1 32-column items); ms_variant[4]:
+ * the tuner's timings (0 before lmfmm_batch_tune).  Any pointer may be NULL. */
+lmfmm_status lmfmm_batch_info(const lmfmm_batch *b, int *merged, int64_t *nwork, int *variant,
+                              double *ms_variant);
+
+const char *lmfmm_batch_last_error(const lmfmm_batch *b);
+void lmfmm_batch_destroy(lmfmm_batch *b);
+
 /* Never NULL; valid until the next call on ctx.  ctx may be NULL (creation
  * errors). */
 const char *lmfmm_last_error(const lmfmm_ctx *ctx);

@@ -169,6 +169,38 @@ lmfmm_status check_mvstatus(lmfmm_ctx *ctx, cudaStream_t st)
     return LMFMM_OK;
 }
 
+// M2L work items of a built context: per geometry and table, runs of pairs
+// giving at most `bn` helical columns (one column per pair for the (s5, 0)
+// table, two for the others); prob tags them for a batched launch.  Returns the
+// column count.
+int64_t m2l_work_items(const lmfmm_ctx *ctx, int bn, int prob, std::vector<M2LWork> &mw)
+{
+    int64_t ncols = 0;
+    for (size_t gi = 0; gi < ctx->geoms.size(); ++gi) {
+        const Geom &g = ctx->geoms[gi];
+        const CompDev &cg = ctx->comps[g.comp];
+        // image maps of the component: the sign of odd degrees flips when the
+        // source (target) side is mirrored an odd number of times
+        const int flags = (((cg.s < 0) != (cg.has_src_refl != 0)) ? 1 : 0) |
+                          (((cg.s < 0) != (cg.has_tgt_refl != 0)) ? 2 : 0);
+        for (int t = 0; t < NTAB; ++t) {
+            const int per = (t == 1) ? bn : bn / 2;
+            for (int64_t q = g.pair0; q < g.pair1; q += per) {
+                M2LWork w{};
+                w.geom = (int)gi;
+                w.t = t;
+                w.flags = flags;
+                w.pair0 = q;
+                w.npair = (int)std::min<int64_t>(per, g.pair1 - q);
+                w.prob = prob;
+                ncols += w.npair * (t == 1 ? 1 : 2);
+                mw.push_back(w);
+            }
+        }
+    }
+    return ncols;
+}
+
 // Tabulate a list of geometries into `tab` (device), batching node factors
 // and Chebyshev integrals through a scratch buffer.
 lmfmm_status tabulate(lmfmm_ctx *ctx, std::vector<GeomDev> &hg, const CompDev *dcomps,
@@ -567,29 +599,8 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
     }
     TRY(dupload(ctx, &d->m2l, ctx->m2l));
     std::vector<M2LWork> mw;
-    int64_t ncols = 0;
-    for (size_t gi = 0; gi < ctx->geoms.size(); ++gi) {
-        const Geom &g = ctx->geoms[gi];
-        const CompDev &cg = ctx->comps[g.comp];
-        // image maps of the component: the sign of odd degrees flips when the
-        // source (target) side is mirrored an odd number of times
-        const int flags = (((cg.s < 0) != (cg.has_src_refl != 0)) ? 1 : 0) |
-                          (((cg.s < 0) != (cg.has_tgt_refl != 0)) ? 2 : 0);
-        for (int t = 0; t < NTAB; ++t) {
-            int bn = d->m2l_kernel >= 2 ? m2l_tc_cols() : f32 ? gemm_cols<float>() : gemm_cols<double>();
-            int per = (t == 1) ? bn : bn / 2;
-            for (int64_t q = g.pair0; q < g.pair1; q += per) {
-                M2LWork w{};
-                w.geom = (int)gi;
-                w.t = t;
-                w.flags = flags;
-                w.pair0 = q;
-                w.npair = (int)std::min<int64_t>(per, g.pair1 - q);
-                ncols += w.npair * (t == 1 ? 1 : 2);
-                mw.push_back(w);
-            }
-        }
-    }
+    const int64_t ncols = m2l_work_items(ctx, d->m2l_kernel >= 2 ? m2l_tc_cols()
+                                                : f32 ? gemm_cols<float>() : gemm_cols<double>(), 0, mw);
     TRY(dupload(ctx, &d->m2lwork, mw));
     d->n_m2lwork = (int64_t)mw.size();
     // translation matrices (exact addition theorem, host)
@@ -796,9 +807,14 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
 }
 
 extern "C++" {
+// stages of one matvec, for the batched launch: the upward pass (gather, P2M,
+// M2M), the M2L (own_m2l = false: only the clearing of the local expansions,
+// the M2L itself runs in the batch's merged launch), the downward pass
+enum { MV_UP = 1, MV_M2L = 2, MV_DOWN = 4, MV_ALL = 7 };
+
 template <typename T>
 static lmfmm_status matvec_t(lmfmm_ctx *ctx, const void *J, int dtype, void *Phi,
-                             cudaStream_t st, bool cj)
+                             cudaStream_t st, bool cj, int parts = MV_ALL, bool own_m2l = true)
 {
     DevState *d = DS(ctx);
     const int p = ctx->prm.p, P = (p + 1) * (p + 1);
@@ -806,6 +822,7 @@ static lmfmm_status matvec_t(lmfmm_ctx *ctx, const void *J, int dtype, void *Phi
     cx<T> *me = (cx<T> *)d->me, *le = (cx<T> *)d->le;
     const cx<T> *tup = (const cx<T> *)d->tup, *tdn = (const cx<T> *)d->tdn;
     int nl = 0;   // kernels launched (launchers skip empty work)
+    if (parts & MV_UP) {
     CK(cudaEventRecord(d->ev[0], st));
     CK(cudaMemsetAsync(d->mvstatus, 0, sizeof(int), st));
     launch_gather_in(N, d->perm, J, dtype, d->qh, cj, st);
@@ -829,10 +846,14 @@ static lmfmm_status matvec_t(lmfmm_ctx *ctx, const void *J, int dtype, void *Phi
                                st);
         nl += w1 > w0;
     }
-    nl += d->n_m2lwork > 0;   // M2L
     CK(cudaEventRecord(d->ev[2], st));
+    }
+    if (parts & MV_M2L) {
+    nl += d->n_m2lwork > 0;   // M2L
     CK(cudaMemsetAsync(le, 0, (size_t)nbox * 3 * P * sizeof(cx<T>), st));
-    if constexpr (std::is_same<T, float>::value) {
+    if (!own_m2l) {
+        // the batch's merged launch applies this problem's M2L
+    } else if constexpr (std::is_same<T, float>::value) {
         if (d->m2l_kernel == 3) {
             CK(launch_m2l_tc2(p, d->n_m2lwork, d->m2lwork, d->geoms, d->m2l, d->ephase, d->tab, d->tscale,
                               me, le, d->yscr, d->nsm, d->mvstatus, st));
@@ -848,6 +869,8 @@ static lmfmm_status matvec_t(lmfmm_ctx *ctx, const void *J, int dtype, void *Phi
                         (const cx<T> *)d->tab, me, le, st);
     }
     CK(cudaEventRecord(d->ev[3], st));
+    }
+    if (parts & MV_DOWN) {
     for (int lev = 1; lev <= ctx->depth; ++lev) {
         if constexpr (std::is_same<T, float>::value) {
             if (d->trans_tc) {
@@ -874,9 +897,10 @@ static lmfmm_status matvec_t(lmfmm_ctx *ctx, const void *J, int dtype, void *Phi
     launch_scatter_out(N, d->perm, d->ph, Phi, dtype, cj, st);
     nl += (d->nleaves > 0) + (d->n_s2twork > 0) + (N > 0);   // L2P, near field, scatter
     CK(cudaEventRecord(d->ev[7], st));
-    CK(cudaGetLastError());
     d->mv_recorded = true;
-    ctx->stats.launches = nl;
+    }
+    CK(cudaGetLastError());
+    if (parts == MV_ALL) ctx->stats.launches = nl;
     return LMFMM_OK;
 }
 
@@ -1054,6 +1078,294 @@ lmfmm_status lmfmm_gradient(lmfmm_ctx *ctx, const void *J, const void *g, int dt
         CK(cudaGetLastError());
     }
     return LMFMM_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batches
+struct lmfmm_batch {
+    std::vector<lmfmm_ctx *> ctxs;
+    int device = 0, p = 0, mixed = 0;
+    bool merged = false;          // every problem on the persistent tensor-core M2L: one merged launch
+    TcProb *dprobs = nullptr;
+    M2LWork *dwork = nullptr;
+    int64_t nwork = 0;
+    int *status = nullptr;
+    int variant = 0;
+    double ms_variant[4] = {0, 0, 0, 0};
+    cudaStream_t cap = nullptr;   // capture stream of the graph
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<const void *> gJ;
+    std::vector<void *> gPhi;
+    int gdtype = -1;
+    std::string err;
+};
+
+namespace {
+
+void batch_drop_graph(lmfmm_batch *b)
+{
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+}
+
+// merged work list of a batch: variant bit 0 interleaves the problems' items
+// round robin (else one problem after the other), bit 1 cuts items to 32
+// helical columns (else 64)
+lmfmm_status batch_work(lmfmm_batch *b, int variant, M2LWork **dst, int64_t *n)
+{
+    std::vector<std::vector<M2LWork>> per(b->ctxs.size());
+    for (size_t i = 0; i < b->ctxs.size(); ++i)
+        m2l_work_items(b->ctxs[i], (variant & 2) ? m2l_tc_cols() / 2 : m2l_tc_cols(), (int)i, per[i]);
+    std::vector<M2LWork> all;
+    if (variant & 1) {
+        for (size_t k = 0;; ++k) {
+            bool any = false;
+            for (auto &v : per)
+                if (k < v.size()) {
+                    all.push_back(v[k]);
+                    any = true;
+                }
+            if (!any) break;
+        }
+    } else {
+        for (auto &v : per) all.insert(all.end(), v.begin(), v.end());
+    }
+    void *q = nullptr;
+    if (cudaMalloc(&q, std::max<size_t>(1, all.size()) * sizeof(M2LWork)) != cudaSuccess) return LMFMM_ERR_OOM;
+    if (!all.empty() && cudaMemcpy(q, all.data(), all.size() * sizeof(M2LWork), cudaMemcpyHostToDevice)) {
+        cudaFree(q);
+        return LMFMM_ERR_CUDA;
+    }
+    *dst = (M2LWork *)q;
+    *n = (int64_t)all.size();
+    return LMFMM_OK;
+}
+
+template <typename T>
+lmfmm_status batch_record(lmfmm_batch *b, const void *const *J, void *const *Phi, int dtype, cudaStream_t st)
+{
+    const size_t n = b->ctxs.size();
+    for (size_t i = 0; i < n; ++i) {
+        lmfmm_status r = matvec_t<T>(b->ctxs[i], J[i], dtype, Phi[i], st, false, MV_UP | MV_M2L, !b->merged);
+        if (r) return r;
+    }
+    if (b->merged) {
+        if (cudaMemsetAsync(b->status, 0, sizeof(int), st) != cudaSuccess) return LMFMM_ERR_CUDA;
+        DevState *d0 = DS(b->ctxs[0]);
+        if (launch_m2l_tc2_batch(b->p, b->nwork, b->dwork, b->dprobs, d0->yscr, d0->nsm, b->status, st) !=
+            cudaSuccess)
+            return LMFMM_ERR_CUDA;
+    }
+    for (size_t i = 0; i < n; ++i) {
+        lmfmm_status r = matvec_t<T>(b->ctxs[i], J[i], dtype, Phi[i], st, false, MV_DOWN);
+        if (r) return r;
+    }
+    return LMFMM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lmfmm_status lmfmm_batch_create(lmfmm_batch **out, lmfmm_ctx *const *ctxs, int n)
+{
+    if (!out || !ctxs || n < 1) {
+        g_err = "batch_create: need n >= 1 contexts";
+        return LMFMM_ERR_ARG;
+    }
+    *out = nullptr;
+    for (int i = 0; i < n; ++i)
+        if (!ctxs[i] || !ctxs[i]->built || ctxs[i]->device != ctxs[0]->device || ctxs[i]->prm.p != ctxs[0]->prm.p ||
+            ctxs[i]->prm.precision != ctxs[0]->prm.precision) {
+            g_err = "batch_create: every context must be built, on one device, with one p and one precision";
+            return LMFMM_ERR_ARG;
+        }
+    if (cudaSetDevice(ctxs[0]->device) != cudaSuccess) return LMFMM_ERR_CUDA;
+    lmfmm_batch *b = new lmfmm_batch();
+    b->ctxs.assign(ctxs, ctxs + n);
+    b->device = ctxs[0]->device;
+    b->p = ctxs[0]->prm.p;
+    b->mixed = ctxs[0]->prm.precision == LMFMM_MIXED;
+    b->merged = true;
+    for (int i = 0; i < n; ++i) b->merged = b->merged && DS(ctxs[i])->m2l_kernel == 3;
+    lmfmm_status rc = LMFMM_OK;
+    if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMalloc((void **)&b->status, sizeof(int)) != cudaSuccess || cudaMemset(b->status, 0, sizeof(int)))
+        rc = LMFMM_ERR_CUDA;
+    if (!rc && b->merged) {
+        std::vector<TcProb> hp(n);
+        for (int i = 0; i < n; ++i) {
+            DevState *d = DS(ctxs[i]);
+            hp[i] = TcProb{d->geoms, d->m2l, d->ephase, d->tab, d->tscale, (const cf *)d->me, (cf *)d->le};
+        }
+        if (cudaMalloc((void **)&b->dprobs, n * sizeof(TcProb)) != cudaSuccess ||
+            cudaMemcpy(b->dprobs, hp.data(), n * sizeof(TcProb), cudaMemcpyHostToDevice) != cudaSuccess)
+            rc = LMFMM_ERR_CUDA;
+        if (!rc) rc = batch_work(b, 0, &b->dwork, &b->nwork);
+    }
+    if (rc) {
+        g_err = "batch_create: device setup failed";
+        lmfmm_batch_destroy(b);
+        return rc;
+    }
+    *out = b;
+    return LMFMM_OK;
+}
+
+lmfmm_status lmfmm_batch_matvec(lmfmm_batch *b, const void *const *J, void *const *Phi, int dtype, void *stream)
+{
+    if (!b) return LMFMM_ERR_ARG;
+    const size_t n = b->ctxs.size();
+    if (!J || !Phi || (dtype != LMFMM_C128 && dtype != LMFMM_C64)) {
+        b->err = "batch_matvec: NULL pointer arrays or bad dtype";
+        return LMFMM_ERR_ARG;
+    }
+    for (size_t i = 0; i < n; ++i)
+        if (!J[i] || !Phi[i]) {
+            b->err = "batch_matvec: NULL buffer";
+            return LMFMM_ERR_ARG;
+        }
+    if (cudaSetDevice(b->device) != cudaSuccess) return LMFMM_ERR_CUDA;
+    const bool same = b->exec && b->gdtype == dtype && std::equal(b->gJ.begin(), b->gJ.end(), J) &&
+                      std::equal(b->gPhi.begin(), b->gPhi.end(), Phi);
+    if (!same) {
+        // record every launch of the batch once, on the capture stream
+        batch_drop_graph(b);
+        if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            b->err = "batch_matvec: stream capture failed to start";
+            return LMFMM_ERR_CUDA;
+        }
+        lmfmm_status rc = b->mixed ? batch_record<float>(b, J, Phi, dtype, b->cap)
+                                   : batch_record<double>(b, J, Phi, dtype, b->cap);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(b->cap, &g);
+        if (rc || e != cudaSuccess || !g) {
+            if (g) cudaGraphDestroy(g);
+            b->err = "batch_matvec: capture of the batch failed";
+            return rc ? rc : LMFMM_ERR_CUDA;
+        }
+        b->graph = g;
+        if (cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess) {
+            batch_drop_graph(b);
+            b->err = "batch_matvec: graph instantiation failed";
+            return LMFMM_ERR_CUDA;
+        }
+        b->gJ.assign(J, J + n);
+        b->gPhi.assign(Phi, Phi + n);
+        b->gdtype = dtype;
+    }
+    if (cudaGraphLaunch(b->exec, (cudaStream_t)stream) != cudaSuccess) {
+        b->err = "batch_matvec: graph launch failed";
+        return LMFMM_ERR_CUDA;
+    }
+    return LMFMM_OK;
+}
+
+lmfmm_status lmfmm_batch_tune(lmfmm_batch *b, void *stream)
+{
+    if (!b) return LMFMM_ERR_ARG;
+    if (!b->merged) {
+        b->err = "batch_tune: the merged M2L needs every problem on the persistent tensor-core kernel";
+        return LMFMM_ERR_UNSUPPORTED;
+    }
+    if (cudaSetDevice(b->device) != cudaSuccess) return LMFMM_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    DevState *d0 = DS(b->ctxs[0]);
+    const int P = (b->p + 1) * (b->p + 1);
+    // defined inputs for the timing runs
+    for (lmfmm_ctx *c : b->ctxs)
+        if (cudaMemsetAsync(DS(c)->me, 0, c->boxes.size() * 3 * (size_t)P * sizeof(cf), st) != cudaSuccess)
+            return LMFMM_ERR_CUDA;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return LMFMM_ERR_CUDA;
+    int best = 0;
+    for (int v = 0; v < 4; ++v) {
+        M2LWork *w = nullptr;
+        int64_t nw = 0;
+        lmfmm_status rc = batch_work(b, v, &w, &nw);
+        if (rc) return rc;
+        float tmin = 1e30f;
+        for (int rep = 0; rep < 4; ++rep) {
+            cudaEventRecord(e0, st);
+            launch_m2l_tc2_batch(b->p, nw, w, b->dprobs, d0->yscr, d0->nsm, b->status, st);
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) tmin = std::min(tmin, ms);   // first run warms the caches
+        }
+        cudaFree(w);
+        b->ms_variant[v] = tmin;
+        if (tmin < b->ms_variant[best]) best = v;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (cudaGetLastError() != cudaSuccess) return LMFMM_ERR_CUDA;
+    M2LWork *w = nullptr;
+    int64_t nw = 0;
+    TRY(batch_work(b, best, &w, &nw));
+    cudaFree(b->dwork);
+    b->dwork = w;
+    b->nwork = nw;
+    b->variant = best;
+    batch_drop_graph(b);   // the next matvec captures the chosen list
+    int f = 0;
+    cudaMemcpy(&f, b->status, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaMemset(b->status, 0, sizeof(int));
+    if (f) {
+        b->err = "batch_tune: a bounded tensor-core wait gave up during the timing runs";
+        return LMFMM_ERR_TIMEOUT;
+    }
+    return LMFMM_OK;
+}
+
+lmfmm_status lmfmm_batch_check(lmfmm_batch *b, void *stream)
+{
+    if (!b) return LMFMM_ERR_ARG;
+    if (cudaSetDevice(b->device) != cudaSuccess || cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess)
+        return LMFMM_ERR_CUDA;
+    int f = 0;
+    if (cudaMemcpy(&f, b->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return LMFMM_ERR_CUDA;
+    for (lmfmm_ctx *c : b->ctxs) {
+        int g = 0;
+        if (cudaMemcpy(&g, DS(c)->mvstatus, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return LMFMM_ERR_CUDA;
+        f |= g;
+    }
+    if (f) {
+        b->err = "batch: a bounded tensor-core wait gave up; the results are incomplete";
+        return LMFMM_ERR_TIMEOUT;
+    }
+    return LMFMM_OK;
+}
+
+lmfmm_status lmfmm_batch_info(const lmfmm_batch *b, int *merged, int64_t *nwork, int *variant, double *ms_variant)
+{
+    if (!b) return LMFMM_ERR_ARG;
+    if (merged) *merged = b->merged;
+    if (nwork) *nwork = b->nwork;
+    if (variant) *variant = b->variant;
+    if (ms_variant)
+        for (int i = 0; i < 4; ++i) ms_variant[i] = b->ms_variant[i];
+    return LMFMM_OK;
+}
+
+const char *lmfmm_batch_last_error(const lmfmm_batch *b) { return b ? b->err.c_str() : g_err.c_str(); }
+
+void lmfmm_batch_destroy(lmfmm_batch *b)
+{
+    if (!b) return;
+    cudaSetDevice(b->device);
+    batch_drop_graph(b);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    cudaFree(b->dprobs);
+    cudaFree(b->dwork);
+    cudaFree(b->status);
+    delete b;
 }
 
 lmfmm_status lmfmm_check(lmfmm_ctx *ctx, void *stream)

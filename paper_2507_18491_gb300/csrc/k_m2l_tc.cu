@@ -666,7 +666,7 @@ __device__ __forceinline__ int v2_ncol(const M2LWork &w, int mode)
 __global__ void __launch_bounds__(V2_THREADS, 1)
     k_m2l_tc2(int p, int mode, int64_t nwork, const M2LWork *work, const GeomDev *geoms, const M2LPair *pairs, const cf *ephase, const int64_t *tsrc, const int64_t *tdst,
               const uint32_t *timg, const float *tscale, const cf *me, cf *le, float *yscr,
-              int *status)
+              int *status, const TcProb *probs)
 {
     extern __shared__ __align__(1024) unsigned char smraw[];
     const int P = (p + 1) * (p + 1);
@@ -692,10 +692,16 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
     auto meta_XS = [&](int slot) { return (float *)(smraw + sp.meta + slot * sp.meta_bytes + sp.sc_off); };
     auto meta_IB = [&](int slot) { return meta_XS(slot) + BN; };
     auto meta_IA = [&](int slot) { return meta_XS(slot) + BN + sp.mm_n; };
+    // the arrays of an item's problem: the launch's own, or a batch entry
+    auto prob = [&](const M2LWork &w) {
+        if (probs) return probs[w.prob];
+        return TcProb{geoms, pairs, ephase, timg, tscale, me, le};
+    };
     // scale block [P + NR] of the table (M2L) or translation matrix of an item
     auto item_scales = [&](const M2LWork &w) {
-        const int64_t ti = mode == 0 ? geoms[w.geom].tab_index * NTAB + w.t : (int64_t)w.geom;
-        return tscale + ti * (int64_t)(P + NR);
+        const TcProb pd = prob(w);
+        const int64_t ti = mode == 0 ? pd.geoms[w.geom].tab_index * NTAB + w.t : (int64_t)w.geom;
+        return pd.tscale + ti * (int64_t)(P + NR);
     };
 
     float *Y = yscr + (size_t)blockIdx.x * NR * 128;   // [complex column][r], complex
@@ -741,8 +747,9 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
             int s = 0;
             for (int64_t it = blockIdx.x; it < nwork && !failed; it += gridDim.x) {
                 const M2LWork w = work[it];
-                const int64_t ti = mode == 0 ? geoms[w.geom].tab_index * NTAB + w.t : (int64_t)w.geom;
-                const unsigned char *src = (const unsigned char *)timg + (size_t)ti * nchunk * sp.CB;
+                const TcProb pd = prob(w);
+                const int64_t ti = mode == 0 ? pd.geoms[w.geom].tab_index * NTAB + w.t : (int64_t)w.geom;
+                const unsigned char *src = (const unsigned char *)pd.img + (size_t)ti * nchunk * sp.CB;
                 for (int c = 0; c < nchunk; ++c) {
                     if (g >= (uint32_t)ST && !tc::mbar_wait(&tempty[s], ph ^ 1, WAIT_POLLS)) {
                         failed = true;
@@ -847,7 +854,8 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
             const uint32_t gr = tc::smem_u32(G + q.pp * MO + p);   // input factors of the column
             const uint32_t ibs = tc::smem_u32(meta_IB(slot));      // input scales of the table
             const float xsc = valid ? meta_XS(slot)[cc] : 0.f;     // scale of the column
-            const cf *src = me + q.in_base;
+            const cf *pme = prob(w).me;
+            const cf *src = pme + q.in_base;
             // this group's chunks of the item: c = cfirst, cfirst + V2_PG, ...
             const int cfirst = (int)((pg + V2_PG - (int)(g0 % V2_PG)) % V2_PG);
             const int nmine = cfirst < nchunk ? (nchunk - cfirst + V2_PG - 1) / V2_PG : 0;
@@ -878,7 +886,7 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
                 for (int h = 0; h < KH; ++h) {
                     const int k = min(KC * ch + b * KH + h, P - 1);
                     const int m = b ? mo[KH + h] : mo[h];
-                    const cf *a = valid ? src + (neg ? k - 2 * m : k) : me;
+                    const cf *a = valid ? src + (neg ? k - 2 * m : k) : pme;
                     v[h] = *(const float2 *)a;
                 }
             };
@@ -960,9 +968,10 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
         // column data of item w into meta slot `slot`, then release it to the producers
         auto fill = [&](const M2LWork &w, int slot) {
             const float *tsc = item_scales(w);
+            const TcProb pd = prob(w);
             v2_fill_scales(P, NR, (int)sp.mm_n, tsc, meta_IB(slot), meta_IA(slot), ea, V2_ET);
             if (mode == 0)
-                v2_fill_meta(p, P, w, pairs, ephase, me, MM, tsc, (w.flags & 1) != 0, (w.flags & 2) != 0,
+                v2_fill_meta(p, P, w, pd.pairs, pd.ephase, pd.me, MM, tsc, (w.flags & 1) != 0, (w.flags & 2) != 0,
                              meta_G(slot), meta_O(slot), meta_cols(slot), meta_XS(slot), ea, V2_ET);
             else
                 v2_fill_trans(p, P, w, tsrc, tdst, me, MM, tsc, meta_G(slot), meta_O(slot), meta_cols(slot),
@@ -1018,6 +1027,7 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
                 break;
             }
             const int ncol = v2_ncol(wc, mode);
+            cf *const ple = prob(wc).le;
             const cf *O = meta_O(slot);
             const V2Col *cols = meta_cols(slot);
             const float *XS = meta_XS(slot), *IA = meta_IA(slot);
@@ -1052,7 +1062,7 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
                         if (r < P) {
                             const cf yy = (ia[i] * ixs) * (Oc[rm[i]] * cf{y[h][i].x, y[h][i].y});
                             // output (nu, mu) with mu = +-mh: index r or r - 2 mh
-                            atomicAdd((float2 *)(le + ob + (kneg ? r - 2 * rm[i] : r)), make_float2(yy.x, yy.y));
+                            atomicAdd((float2 *)(ple + ob + (kneg ? r - 2 * rm[i] : r)), make_float2(yy.x, yy.y));
                         }
                     }
                 }
@@ -1276,7 +1286,20 @@ static cudaError_t launch_tc2(int p, int mode, int64_t nwork, const M2LWork *wor
     const size_t smem = std::max<size_t>(v2_plan(p).total, 116 * 1024);
     k_m2l_tc2<<<(unsigned)grid, V2_THREADS, smem, st>>>(p, mode, nwork, work, geoms, pairs, ephase, tsrc,
                                                         tdst, (const uint32_t *)img, scales, in, out, yscr,
-                                                        status);
+                                                        status, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_m2l_tc2_batch(int p, int64_t nwork, const M2LWork *work, const TcProb *probs, float *yscr,
+                                 int nsm, int *status, cudaStream_t st)
+{
+    if (nwork <= 0) return cudaSuccess;
+    if (!m2l_tc2_supported(p) || nsm < 1) return cudaErrorInvalidValue;
+    const int64_t grid = std::min<int64_t>(nwork, (int64_t)nsm);
+    const size_t smem = std::max<size_t>(v2_plan(p).total, 116 * 1024);
+    k_m2l_tc2<<<(unsigned)grid, V2_THREADS, smem, st>>>(p, 0, nwork, work, nullptr, nullptr, nullptr, nullptr,
+                                                        nullptr, nullptr, nullptr, nullptr, nullptr, yscr,
+                                                        status, probs);
     return cudaGetLastError();
 }
 

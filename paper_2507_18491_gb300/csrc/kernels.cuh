@@ -57,6 +57,20 @@ struct M2LWork {        // one M2L table applied to a chunk of pairs of one geom
     int geom, t, npair;
     int flags;          // bit 0: odd input degrees change sign, bit 1: odd output degrees
     int64_t pair0;
+    int prob, pad;      // problem of a batched launch (TcProb index), else 0
+};
+
+// per-problem arrays of a batched persistent M2L launch (k_m2l_tc2): one
+// problem's geometries, pairs, pair phases, table image and scales, and its
+// multipole / local expansions
+struct TcProb {
+    const GeomDev *geoms;
+    const M2LPair *pairs;
+    const cf *ephase;
+    const void *img;
+    const float *tscale;
+    const cf *me;
+    cf *le;
 };
 
 // k_tab.cu
@@ -126,6 +140,10 @@ void launch_tile_tables(int p, int64_t g0, int64_t ng, const GeomDev *geoms, con
 cudaError_t launch_m2l_tc2(int p, int64_t nwork, const M2LWork *work, const GeomDev *geoms,
                            const M2LPair *pairs, const cf *ephase, const void *img, const float *scales,
                            const cf *me, cf *le, float *yscr, int nsm, int *status, cudaStream_t st);
+// the M2L of several problems (same p) in one persistent launch: work items
+// carry their problem index into probs (device array)
+cudaError_t launch_m2l_tc2_batch(int p, int64_t nwork, const M2LWork *work, const TcProb *probs, float *yscr,
+                                 int nsm, int *status, cudaStream_t st);
 // M2M or L2L on the same kernel: items M2LWork{geom = translation group, t = 0,
 // npair, pair0} over pairs (tsrc[q], tdst[q]), 3 helical columns each; img holds
 // one tiled matrix per group (tile_matrix_tc2, tc2_matrix_bytes(p) each) and

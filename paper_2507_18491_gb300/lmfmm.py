@@ -54,7 +54,9 @@ EXPORTS = ["lmfmm_default_params", "lmfmm_create", "lmfmm_set_layers", "lmfmm_se
            "lmfmm_matvec_adjoint", "lmfmm_matvec_transpose", "lmfmm_gradient", "lmfmm_check", "lmfmm_test_set_status", "lmfmm_direct",
            "lmfmm_direct_noalloc", "lmfmm_densities", "lmfmm_m2l_table", "lmfmm_translation_matrix",
            "lmfmm_free_m2l_table",
-           "lmfmm_get_stats", "lmfmm_last_error", "lmfmm_destroy"]
+           "lmfmm_get_stats", "lmfmm_last_error", "lmfmm_destroy", "lmfmm_batch_create",
+           "lmfmm_batch_matvec", "lmfmm_batch_tune", "lmfmm_batch_check", "lmfmm_batch_info",
+           "lmfmm_batch_last_error", "lmfmm_batch_destroy"]
 
 
 class LmfmmError(RuntimeError):
@@ -101,6 +103,14 @@ def load():
         "lmfmm_get_stats": [P, ctypes.POINTER(Stats)],
         "lmfmm_last_error": [P],
         "lmfmm_destroy": [P],
+        "lmfmm_batch_create": [ctypes.POINTER(P), ctypes.POINTER(P), i],
+        "lmfmm_batch_matvec": [P, ctypes.POINTER(P), ctypes.POINTER(P), i, P],
+        "lmfmm_batch_tune": [P, P],
+        "lmfmm_batch_check": [P, P],
+        "lmfmm_batch_info": [P, ctypes.POINTER(i), ctypes.POINTER(i64), ctypes.POINTER(i),
+                             ctypes.POINTER(d)],
+        "lmfmm_batch_last_error": [P],
+        "lmfmm_batch_destroy": [P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -108,6 +118,8 @@ def load():
         f.restype = ctypes.c_int
     lib.lmfmm_last_error.restype = ctypes.c_char_p
     lib.lmfmm_destroy.restype = None
+    lib.lmfmm_batch_last_error.restype = ctypes.c_char_p
+    lib.lmfmm_batch_destroy.restype = None
     _lib = lib
     return lib
 
@@ -438,3 +450,58 @@ class _LazyFn:
 
 
 _ReactionFieldFn = _LazyFn
+
+
+class Batch:
+    """Several built Operators applied together (lmfmm_batch_*): one CUDA graph
+    per set of buffers, the M2L of all problems in one persistent launch."""
+
+    def __init__(self, ops):
+        self.ops = list(ops)
+        arr = (ctypes.c_void_p * len(self.ops))(*[o.ctx.value for o in self.ops])
+        h = ctypes.c_void_p()
+        rc = load().lmfmm_batch_create(ctypes.byref(h), arr, len(self.ops))
+        if rc != OK:
+            raise LmfmmError(rc, load().lmfmm_batch_last_error(None).decode())
+        self.h = h
+
+    def _check(self, rc):
+        if rc != OK:
+            raise LmfmmError(rc, load().lmfmm_batch_last_error(self.h).decode())
+
+    def matvec(self, Js, outs, stream=None):
+        n = len(self.ops)
+        codes = [_field(J)[1] for J in Js]
+        for J, o in zip(Js, outs):
+            _field(o, like=J)
+        if len(set(codes)) != 1 or len(Js) != n or len(outs) != n:
+            raise ValueError("one J and one output per problem, all of one dtype")
+        pj = (ctypes.c_void_p * n)(*[J.data_ptr() for J in Js])
+        po = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
+        self._keep = (pj, po)
+        self._check(load().lmfmm_batch_matvec(self.h, pj, po, codes[0], _stream(stream)))
+        return outs
+
+    def tune(self, stream=None):
+        self._check(load().lmfmm_batch_tune(self.h, _stream(stream)))
+
+    def check(self, stream=None):
+        self._check(load().lmfmm_batch_check(self.h, _stream(stream)))
+
+    def info(self):
+        m, v = ctypes.c_int(), ctypes.c_int()
+        nw = ctypes.c_int64()
+        ms = (ctypes.c_double * 4)()
+        self._check(load().lmfmm_batch_info(self.h, ctypes.byref(m), ctypes.byref(nw), ctypes.byref(v), ms))
+        return {"merged": bool(m.value), "nwork": nw.value, "variant": v.value, "ms_variant": list(ms)}
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().lmfmm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -183,3 +183,24 @@ def accuracy_sample(w, n_targets, n_random_sources, n_neighbours, band, seed=11,
         src.append(np.array([t]))
     sources = np.unique(np.concatenate(src)).astype(np.int64)
     return targets, sources
+
+
+def batch_problems(n_problems=64, seed=1004, n_min=2048, n_max=65536, k_min=0.5, k_max=4.0, p=8):
+    """Many layered problems of uneven size and frequency (the batched
+    configuration): each has two or three layers (interfaces z = 0 and, for
+    three, a second one at -U[0.8, 1.6]), layer wavenumbers U[k_min, k_max]
+    with a small loss U[0, 0.02] i, N ~ U[n_min, n_max] points split evenly
+    over the layers (uniform in [-1,1]^2 x each layer, 0.1 from interfaces,
+    unbounded layers cut at height 1) and complex64 currents."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_problems):
+        nl = int(rng.integers(2, 4))
+        d = np.array([0.0]) if nl == 2 else np.array([0.0, -rng.uniform(0.8, 1.6)])
+        k = rng.uniform(k_min, k_max, nl) + 1j * rng.uniform(0.0, 0.02, nl)
+        n = int(rng.integers(n_min, n_max + 1))
+        counts = [n // nl + (1 if j < n % nl else 0) for j in range(nl)]
+        xyz = points_in_layers(rng, d, counts, margin=0.1, xy=1.0, height=1.0)
+        out.append(Workload("batch_%d_n%d" % (i, n), d, k.astype(complex), xyz,
+                            _currents(rng, n, True), p=p, depth=-1, dtype="c64"))
+    return out
