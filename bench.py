@@ -58,9 +58,9 @@ def tensor_peak(tf32):
 def workload(name, seed_shift=0):
     from paper_2507_18491_gb300 import workloads as W
     if name == "four_layer":
-        return W.four_layer_clusters(seed=1005 + seed_shift), dict(depth=6, theta=0.55)
+        return W.four_layer_clusters(seed=1005 + seed_shift), dict(depth=6, theta=0.5)
     if name == "three_layer":
-        return W.three_layer(seed=1002 + seed_shift), dict(depth=5, theta=0.55)
+        return W.three_layer(seed=1002 + seed_shift), dict(depth=5, theta=0.45)
     if name == "four_layer_small":
         return W.four_layer_clusters(n=131072, seed=1005 + seed_shift), dict(depth=4, theta=0.55)
     if name == "three_layer_small":
@@ -254,6 +254,7 @@ def main():
                     help="skip the FP64-form comparison run of the default (mixed) bench")
     ap.add_argument("--workload", default="four_layer")
     ap.add_argument("--p", type=int, default=0)
+    ap.add_argument("--theta", type=float, default=0.0, help="admissibility (default: the workload's)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--tensor-cores", type=int, default=3,
                     help="tensor_cores option of the mixed form: 3 = M2L, M2M and L2L on the "
@@ -269,6 +270,8 @@ def main():
     torch.cuda.set_device(dev)
     B.build()
     w, opt = workload(args.workload, seed_shift=rank)
+    if args.theta:
+        opt["theta"] = args.theta
     p = args.p or w.p
     prec = lmfmm.FP64 if args.precision == "fp64" else lmfmm.MIXED
     t0 = time.time()

@@ -3,6 +3,7 @@
 // and the matvec pipeline P2M -> M2M -> M2L -> L2L -> L2P (+ S2T).
 #include <algorithm>
 #include <chrono>
+#include <map>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -39,9 +40,7 @@ struct DevState {
     int64_t *tchild = nullptr, *tparent = nullptr;
     GemmWork *gwork = nullptr;
     std::vector<int64_t> gwork_off;  // per child level: [off[l], off[l+1])
-    void *tupi = nullptr, *tdni = nullptr;    // persistent kernel: tiled translation matrices (fp16 x 2)
-    float *tsc_up = nullptr, *tsc_dn = nullptr;   // ... and their row / column scales
-    float *tscale = nullptr;                  // persistent kernel: row / column scales of the table image
+    void *tupi = nullptr, *tdni = nullptr;    // persistent kernel: tiled translation matrices (bf16 x 3)
     M2LWork *twork = nullptr;        // persistent kernel: translation items, per child level
     bool trans_tc = false;           // M2M / L2L on the persistent kernel (tensor_cores = 3)
     std::vector<int64_t> twork_off;
@@ -560,8 +559,7 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
         if (d->m2l_kernel == 3) {
             unsigned char *img = nullptr;
             TRY(dalloc(ctx, &img, m2l_tc2_image_bytes(p, (int64_t)hg.size())));
-            TRY(dalloc(ctx, &d->tscale, m2l_tc2_scale_floats(p, (int64_t)hg.size() * NTAB)));
-            launch_tile_tables(p, 0, (int64_t)hg.size(), d->geoms, d->comps, tab64, img, d->tscale, st);
+            launch_tile_tables(p, 0, (int64_t)hg.size(), d->geoms, d->comps, tab64, img, st);
             CK(cudaGetLastError());
             CK(cudaStreamSynchronize(st));
             dfree(ctx, tab64);
@@ -678,18 +676,15 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
         if (d->trans_tc) {
             // M2M / L2L on the persistent tensor-core kernel: tiled bf16 three-piece
             // images of the scaled FP64 matrices, items of 21 pairs (63 helical columns)
-            const size_t mw = tc2_matrix_bytes(p) / 4, ns = m2l_tc2_scale_floats(p, 1);
+            const size_t mw = tc2_matrix_bytes(p) / 4;
             std::vector<uint32_t> iu(ngr * mw), id(ngr * mw);
-            std::vector<float> su(ngr * ns), sd(ngr * ns);
             for (size_t i = 0; i < ngr; ++i) {
-                tile_matrix_tc2(p, &hup[i * P * P], &iu[i * mw], &su[i * ns]);
-                tile_matrix_tc2(p, &hdn[i * P * P], &id[i * mw], &sd[i * ns]);
+                tile_matrix_tc2(p, &hup[i * P * P], &iu[i * mw]);
+                tile_matrix_tc2(p, &hdn[i * P * P], &id[i * mw]);
             }
             uint32_t *a1 = nullptr, *a2 = nullptr;
             TRY(dupload(ctx, &a1, iu));
             TRY(dupload(ctx, &a2, id));
-            TRY(dupload(ctx, &d->tsc_up, su));
-            TRY(dupload(ctx, &d->tsc_dn, sd));
             d->tupi = a1;
             d->tdni = a2;
             std::vector<M2LWork> tw;
@@ -835,7 +830,7 @@ static lmfmm_status matvec_t(lmfmm_ctx *ctx, const void *J, int dtype, void *Phi
         if constexpr (std::is_same<T, float>::value) {
             if (d->trans_tc) {
                 int64_t w0 = d->twork_off[lev], w1 = d->twork_off[lev + 1];
-                CK(launch_trans_tc2(p, w1 - w0, d->twork + w0, d->tchild, d->tparent, d->tupi, d->tsc_up, me, me,
+                CK(launch_trans_tc2(p, w1 - w0, d->twork + w0, d->tchild, d->tparent, d->tupi, me, me,
                                     d->yscr, d->nsm, d->mvstatus, st));
                 nl += w1 > w0;
                 continue;
@@ -855,7 +850,7 @@ static lmfmm_status matvec_t(lmfmm_ctx *ctx, const void *J, int dtype, void *Phi
         // the batch's merged launch applies this problem's M2L
     } else if constexpr (std::is_same<T, float>::value) {
         if (d->m2l_kernel == 3) {
-            CK(launch_m2l_tc2(p, d->n_m2lwork, d->m2lwork, d->geoms, d->m2l, d->ephase, d->tab, d->tscale,
+            CK(launch_m2l_tc2(p, d->n_m2lwork, d->m2lwork, d->geoms, d->m2l, d->ephase, d->tab,
                               me, le, d->yscr, d->nsm, d->mvstatus, st));
         }
         else if (d->m2l_kernel == 2)
@@ -875,7 +870,7 @@ static lmfmm_status matvec_t(lmfmm_ctx *ctx, const void *J, int dtype, void *Phi
         if constexpr (std::is_same<T, float>::value) {
             if (d->trans_tc) {
                 int64_t w0 = d->twork_off[lev], w1 = d->twork_off[lev + 1];
-                CK(launch_trans_tc2(p, w1 - w0, d->twork + w0, d->tparent, d->tchild, d->tdni, d->tsc_dn, le, le,
+                CK(launch_trans_tc2(p, w1 - w0, d->twork + w0, d->tparent, d->tchild, d->tdni, le, le,
                                     d->yscr, d->nsm, d->mvstatus, st));
                 nl += w1 > w0;
                 continue;
@@ -1200,7 +1195,7 @@ lmfmm_status lmfmm_batch_create(lmfmm_batch **out, lmfmm_ctx *const *ctxs, int n
         std::vector<TcProb> hp(n);
         for (int i = 0; i < n; ++i) {
             DevState *d = DS(ctxs[i]);
-            hp[i] = TcProb{d->geoms, d->m2l, d->ephase, d->tab, d->tscale, (const cf *)d->me, (cf *)d->le};
+            hp[i] = TcProb{d->geoms, d->m2l, d->ephase, d->tab, (const cf *)d->me, (cf *)d->le};
         }
         if (cudaMalloc((void **)&b->dprobs, n * sizeof(TcProb)) != cudaSuccess ||
             cudaMemcpy(b->dprobs, hp.data(), n * sizeof(TcProb), cudaMemcpyHostToDevice) != cudaSuccess)

@@ -35,7 +35,6 @@
 #include <vector>
 
 #include <cuda_bf16.h>
-#include <cuda_fp16.h>
 
 #include "kernels.cuh"
 #include "m2l_cols.cuh"
@@ -407,9 +406,9 @@ namespace {
 
 constexpr int V2_KS = 2;           // MMA K-steps (16 real K each) per ring chunk
 constexpr int V2_KC = 8 * V2_KS;   // complex inputs per ring chunk
-constexpr int V2_NPC = 2;          // fp16 pieces per value
+constexpr int V2_NPC = 3;          // bf16 pieces per value
 constexpr int V2_XW = 8 * V2_NPC * V2_KS;   // tensor-memory columns of an X chunk
-constexpr int V2_SX = 4;           // X ring slots
+constexpr int V2_SX = 3;           // X ring slots
 constexpr int V2_ST_MAX = 16;      // table ring slots (shared memory)
 constexpr int V2_PG = 2;           // producer groups (alternate chunks)
 constexpr int V2_D = 2;            // chunks of a group prefetched into registers
@@ -429,8 +428,7 @@ struct V2Col {
 };
 
 struct V2Plan {
-    uint32_t NR, nchunk, SB, CB, ST, MO, g_bytes, cols_bytes, sc_off, meta_bytes, meta, tabs, mm_n, dtile, bars,
-        total;
+    uint32_t NR, nchunk, SB, CB, ST, MO, g_bytes, cols_bytes, meta_bytes, meta, tabs, mm_n, dtile, bars, total;
 };
 
 __host__ __device__ inline V2Plan v2_plan(int p)
@@ -439,14 +437,13 @@ __host__ __device__ inline V2Plan v2_plan(int p)
     V2Plan s;
     s.NR = (uint32_t)((P + 15) & ~15);
     s.nchunk = (uint32_t)(((P + 7) / 8 + V2_KS - 1) / V2_KS);   // chunks of V2_KS K-steps
-    s.SB = s.NR * 32 * V2_NPC;                      // image of a K-step: V2_NPC planes of NR rows x 16 fp16
+    s.SB = s.NR * 32 * V2_NPC;                      // image of a K-step: V2_NPC planes of NR rows x 16 bf16
     s.CB = V2_KS * s.SB;
     s.MO = 2 * p + 1;                               // orders -p..p
     s.g_bytes = BN * s.MO * 8;                      // one factor table: [64][2p+1] complex
     s.cols_bytes = BN * (uint32_t)sizeof(V2Col);
+    s.meta_bytes = 2 * s.g_bytes + s.cols_bytes;    // G, O, column records
     s.mm_n = V2_KC * s.nchunk;                      // order table, whole chunks (>= P)
-    s.sc_off = 2 * s.g_bytes + s.cols_bytes;        // scales: column [64], input [mm_n], row [NR]
-    s.meta_bytes = s.sc_off + (BN + s.mm_n + s.NR) * 4;
     const uint32_t dtile_bytes = V2_EW * 16 * V2_DS * 4;   // per epilogue warp: 16 rows x 32 lanes
     const uint32_t fixed =
         2 * s.meta_bytes + 2 * s.mm_n + 32 + dtile_bytes + 16 + (2 * V2_ST_MAX + 2 * V2_SX + 12) * 8 + 16;
@@ -466,12 +463,6 @@ __device__ __forceinline__ cf lds_cf(uint32_t a)
     asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
     return v;
 }
-__device__ __forceinline__ float lds_f32(uint32_t a)
-{
-    float v;
-    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
-    return v;
-}
 __device__ __forceinline__ uint4 lds_u4(uint32_t a)
 {
     uint4 v;
@@ -479,25 +470,21 @@ __device__ __forceinline__ uint4 lds_u4(uint32_t a)
     return v;
 }
 
-// two-piece fp16 split of a pair, x ~ h1 + h2 per component (h1 = fp16(x),
-// h2 = fp16(x - h1): 22 significant bits for |x| in [2^-3, 2^15], an absolute
-// floor of 2^-25 below); word j holds piece j, lo in the low half
-__device__ __forceinline__ void v2_split_f16(float lo, float hi, uint32_t (&w)[V2_NPC])
+// three-piece bf16 split of a pair, x ~ b1 + b2 + b3 per component (b1 =
+// bf16(x), b2 = bf16(x - b1), b3 = bf16(x - b1 - b2): 24 significant bits,
+// FP32's exponent range); word j holds piece j, lo in the low half
+__device__ __forceinline__ void v2_split_bf16(float lo, float hi, uint32_t (&w)[V2_NPC])
 {
-    const __half2 h1 = __floats2half2_rn(lo, hi);
-    const float2 f = __half22float2(h1);
-    const __half2 h2 = __floats2half2_rn(lo - f.x, hi - f.y);
-    w[0] = *(const uint32_t *)&h1;
-    w[1] = *(const uint32_t *)&h2;
-}
-
-// power of two 2^floor(log2 x) of a positive finite x (0 for x = 0)
-__host__ __device__ inline double pow2_floor(double x)
-{
-    if (!(x > 0)) return 0.0;
-    int e;
-    frexp(x, &e);   // x = f 2^e, f in [0.5, 1)
-    return ldexp(1.0, e - 1);
+    float2 r{lo, hi};
+#pragma unroll
+    for (int j = 0; j < V2_NPC; ++j) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(r.x, r.y);
+        w[j] = *(const uint32_t *)&h;
+        if (j + 1 < V2_NPC) {
+            const float2 f = __bfloat1622float2(h);
+            r = float2{r.x - f.x, r.y - f.y};
+        }
+    }
 }
 
 // i^k v, exact
@@ -511,67 +498,16 @@ __device__ __forceinline__ cf mul_ipow(int k, cf v)
     }
 }
 
-// Scales of the fp16 form (all powers of two, so exact).  The stored table
-// image holds T' = diag(a) T diag(b) (a_r, b_k of its rows and input columns,
-// set at build time: b equilibrates the columns, a brings every row maximum to
-// 2^14), and tsc[] of the table holds ib_k = 1/b_k (k < P) then ia_r = 1/a_r
-// (r < NR).  A work item column c gets its own xs_c = 2^10 / (power of two of
-// max_k |X_k| ib_k), so that the split inputs X'_k = X_k ib_k xs_c sit in
-// fp16's full-precision range whatever the box's charge; the epilogue undoes
-// it: y_r = ia_r / xs_c * (T' X')_r.
-__device__ __forceinline__ float v2_col_scale(float mx)
-{
-    if (!(mx > 0.f) || !(mx < 3e38f)) return 1.f;
-    int e;
-    frexpf(mx, &e);
-    return ldexpf(1.f, 11 - e);
-}
-
-// column record and scale of one column (warp-uniform call; the lanes share the
-// maximum over the inputs k = lane + 32 i)
-__device__ __forceinline__ void v2_col_record(int P, const V2Col &q, bool valid, const cf *in, const short *MM,
-                                              const float *tsc, int lane, int col, V2Col *cols, float *XS)
-{
-    float mx = 0.f;
-    if (valid) {
-        const bool neg = q.kap < 0;
-#pragma unroll
-        for (int i = 0; i < V2_RJ; ++i) {
-            const int k = lane + 32 * i;
-            if (k < P) {
-                const int idx = neg ? k - 2 * MM[k] : k;
-                const cf v = in[q.in_base + idx];
-                mx = fmaxf(mx, (fabsf(v.x) + fabsf(v.y)) * tsc[k]);
-            }
-        }
-    }
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane == 0) {
-        cols[col] = q;
-        XS[col] = v2_col_scale(mx);
-    }
-}
-
-// the table's input and row scales into the item's meta slot
-__device__ __forceinline__ void v2_fill_scales(int P, int NR, int mm_n, const float *tsc, float *IB, float *IA,
-                                               int tid, int nthr)
-{
-    for (int k = tid; k < mm_n; k += nthr) IB[k] = k < P ? tsc[k] : 0.f;
-    for (int r = tid; r < NR; r += nthr) IA[r] = tsc[P + r];
-}
-
 // per-item column data, all exact transforms of the pair phases
 // E[pp][d] = e^{i d phi} (FP64-computed, stored FP32):
 //   input factors  G[pp][m'] = i^m' f_s^m' E[m'],
 //   output factors O[col][mh] = coef i^(1+kappa) (-i)^mu f_t^mu E[kappa - mu],
 //   mu = +-mh (sign of kappa), coef in {1/2, 1, -1/2};
-// the column records and scales.  One warp per pair or column row, one lane
-// per order (2p+1 <= 32), so that the fill has no division and no divergence.
+// and the column records.  One warp per pair or column row, one lane per
+// order (2p+1 <= 32), so that the fill has no division and no divergence.
 __device__ __forceinline__ void v2_fill_meta(int p, int P, const M2LWork &w, const M2LPair *pairs,
-                                             const cf *ephase, const cf *me, const short *MM, const float *tsc,
-                                             bool flip_in, bool flip_out, cf *G, cf *O, V2Col *cols, float *XS,
-                                             int tid, int nthr)
+                                             const cf *ephase, bool flip_in, bool flip_out, cf *G, cf *O,
+                                             V2Col *cols, int tid, int nthr)
 {
     const int MO = 2 * p + 1, MW = 2 * p + 5;
     const int t = w.t, ncpp = (t == 1) ? 1 : 2, ncol = w.npair * ncpp;
@@ -580,6 +516,8 @@ __device__ __forceinline__ void v2_fill_meta(int p, int P, const M2LWork &w, con
     // rows per warp: at most RB (npair, ncol <= 64 over nw >= 8 warps); every
     // global load of the fill is issued before the first use
     constexpr int RB = 8;
+    M2LPair pr{};
+    if (tid < ncol) pr = pairs[w.pair0 + (ncpp == 1 ? tid : tid >> 1)];
     cf vg[RB], vo[RB];
     if (lane < MO) {
 #pragma unroll
@@ -615,43 +553,38 @@ __device__ __forceinline__ void v2_fill_meta(int p, int P, const M2LWork &w, con
             O[col * MO + lane] = cf0 * mul_ipow(1 + cs.kap - mu, vo[i]);
         }
     }
-    for (int col = wi; col < BN; col += nw) {
+    static_assert(BN <= V2_ET, "one column record per epilogue thread");
+    if (tid < BN) {
         V2Col q{};
-        const bool valid = col < ncol;
-        if (valid) {
-            const ColSpec &cs = c_cols[t][ncpp == 1 ? 0 : col & 1];
-            const M2LPair pr = pairs[w.pair0 + (ncpp == 1 ? col : col >> 1)];
+        if (tid < ncol) {
+            const ColSpec &cs = c_cols[t][ncpp == 1 ? 0 : tid & 1];
             q.in_base = (pr.src * 3 + cs.vin) * (int64_t)P;
             q.out_base = (pr.tgt * 3 + cs.vout) * (int64_t)P;
-            q.pp = ncpp == 1 ? col : col >> 1;
+            q.pp = ncpp == 1 ? tid : tid >> 1;
             q.kap = cs.kap;
         }
-        v2_col_record(P, q, valid, me, MM, tsc, lane, col, cols, XS);
+        cols[tid] = q;
     }
 }
 
 __device__ __forceinline__ void v2_fill_trans(int p, int P, const M2LWork &w, const int64_t *tsrc,
-                                              const int64_t *tdst, const cf *in, const short *MM,
-                                              const float *tsc, cf *G, cf *O, V2Col *cols, float *XS, int tid,
-                                              int nthr)
+                                              const int64_t *tdst, cf *G, cf *O, V2Col *cols, int tid, int nthr)
 {
     const int MO = 2 * p + 1, ncol = 3 * w.npair;
-    const int lane = tid & 31, wi = tid >> 5, nw = nthr >> 5;
     for (int e = tid; e < BN * MO; e += nthr) {
         G[e] = cf{1.f, 0.f};
         O[e] = cf{1.f, 0.f};
     }
-    for (int col = wi; col < BN; col += nw) {
+    for (int col = tid; col < BN; col += nthr) {
         V2Col q{};
-        const bool valid = col < ncol;
-        if (valid) {
+        if (col < ncol) {
             const int pp = col / 3, v = col - 3 * pp;
             q.in_base = (tsrc[w.pair0 + pp] * 3 + v) * (int64_t)P;
             q.out_base = (tdst[w.pair0 + pp] * 3 + v) * (int64_t)P;
             q.pp = pp;
             q.kap = 0;
         }
-        v2_col_record(P, q, valid, in, MM, tsc, lane, col, cols, XS);
+        cols[col] = q;
     }
 }
 
@@ -665,7 +598,7 @@ __device__ __forceinline__ int v2_ncol(const M2LWork &w, int mode)
 
 __global__ void __launch_bounds__(V2_THREADS, 1)
     k_m2l_tc2(int p, int mode, int64_t nwork, const M2LWork *work, const GeomDev *geoms, const M2LPair *pairs, const cf *ephase, const int64_t *tsrc, const int64_t *tdst,
-              const uint32_t *timg, const float *tscale, const cf *me, cf *le, float *yscr,
+              const uint32_t *timg, const cf *me, cf *le, float *yscr,
               int *status, const TcProb *probs)
 {
     extern __shared__ __align__(1024) unsigned char smraw[];
@@ -688,20 +621,11 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
     auto meta_cols = [&](int slot) {
         return (V2Col *)(smraw + sp.meta + slot * sp.meta_bytes + 2 * sp.g_bytes);
     };
-    // scales of the item (see v2_col_scale): column xs [BN], input ib [mm_n], row ia [NR]
-    auto meta_XS = [&](int slot) { return (float *)(smraw + sp.meta + slot * sp.meta_bytes + sp.sc_off); };
-    auto meta_IB = [&](int slot) { return meta_XS(slot) + BN; };
-    auto meta_IA = [&](int slot) { return meta_XS(slot) + BN + sp.mm_n; };
+
     // the arrays of an item's problem: the launch's own, or a batch entry
     auto prob = [&](const M2LWork &w) {
         if (probs) return probs[w.prob];
-        return TcProb{geoms, pairs, ephase, timg, tscale, me, le};
-    };
-    // scale block [P + NR] of the table (M2L) or translation matrix of an item
-    auto item_scales = [&](const M2LWork &w) {
-        const TcProb pd = prob(w);
-        const int64_t ti = mode == 0 ? pd.geoms[w.geom].tab_index * NTAB + w.t : (int64_t)w.geom;
-        return pd.tscale + ti * (int64_t)(P + NR);
+        return TcProb{geoms, pairs, ephase, timg, me, le};
     };
 
     float *Y = yscr + (size_t)blockIdx.x * NR * 128;   // [complex column][r], complex
@@ -772,7 +696,7 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
     } else if (warp == V2_WMMA) {
         // ------------------------------------------------ MMA issue
         if (lane == 0) {
-            const uint32_t idesc = tc::idesc_f16(128, NR);
+            const uint32_t idesc = tc::idesc_bf16(128, NR);
             // descriptor of ring slot 0; the address field counts 16-byte units,
             // so slot, K-step and lo-plane offsets add to it directly
             const uint64_t dring0 = tc::sdesc(tc::smem_u32(smraw), 128, 256);
@@ -795,13 +719,16 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
                     tc::fence_after();
 #pragma unroll
                     for (int u = 0; u < V2_KS; ++u) {
-                        // pieces 1, 2 of X (tensor memory) and of the table (shared memory)
-                        const uint32_t a1 = aslot + 8 * V2_NPC * u, a2 = a1 + 8;
-                        const uint64_t b1 = dslot + u * d_sb, b2 = b1 + d_pl;
+                        // pieces 1, 2, 3 of X (tensor memory) and of the table (shared memory)
+                        const uint32_t a1 = aslot + 8 * V2_NPC * u, a2 = a1 + 8, a3 = a1 + 16;
+                        const uint64_t b1 = dslot + u * d_sb, b2 = b1 + d_pl, b3 = b2 + d_pl;
                         const uint32_t acc = (c > 0 || u > 0) ? 1u : 0u;
                         tc::mma_f16_ta(tbase, a1, b1, idesc, acc);        // 1 x 1: large accumulator
-                        tc::mma_f16_ta(tbase + NR, a1, b2, idesc, acc);   // 1 x 2 + 2 x 1: small accumulator
+                        tc::mma_f16_ta(tbase + NR, a1, b2, idesc, acc);   // the rest: small accumulator
                         tc::mma_f16_ta(tbase + NR, a2, b1, idesc, 1u);
+                        tc::mma_f16_ta(tbase + NR, a1, b3, idesc, 1u);
+                        tc::mma_f16_ta(tbase + NR, a2, b2, idesc, 1u);
+                        tc::mma_f16_ta(tbase + NR, a3, b1, idesc, 1u);
                     }
                     tc::commit(&tempty[st]);
                     tc::commit(&xempty[sx]);
@@ -852,8 +779,6 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
             if (valid) q = cols[cc];
             const bool neg = q.kap < 0;
             const uint32_t gr = tc::smem_u32(G + q.pp * MO + p);   // input factors of the column
-            const uint32_t ibs = tc::smem_u32(meta_IB(slot));      // input scales of the table
-            const float xsc = valid ? meta_XS(slot)[cc] : 0.f;     // scale of the column
             const cf *pme = prob(w).me;
             const cf *src = pme + q.in_base;
             // this group's chunks of the item: c = cfirst, cfirst + V2_PG, ...
@@ -915,16 +840,15 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
                         cf v{0.f, 0.f};
                         if (valid && KC * ch + kk < P) {
                             const int m = b ? mo[KH + h] : mo[h];
-                            const float sk = lds_f32(ibs + 4 * (KC * ch + kk)) * xsc;
-                            v = sk * (lds_cf(gr + 8 * (neg ? -m : m)) * cf{pre[u][h].x, pre[u][h].y});
+                            v = lds_cf(gr + 8 * (neg ? -m : m)) * cf{pre[u][h].x, pre[u][h].y};
                         }
                         mine[h] = v;
                     }
                     // tensor-memory slot: per K-step of 16 real K (8 inputs) 8 columns of
-                    // fp16 pairs for each of the 2 pieces; input kk -> (row 2c: Re, -Im;
+                    // bf16 pairs for each of the 3 pieces; input kk -> (row 2c: Re, -Im;
                     // row 2c+1: Im, Re), even K in the low half
-                    // One K-step at a time (16 words live), one 16-column store each.
-                    static_assert(V2_KS == 2 && V2_NPC == 2, "two K-steps of 16 columns per chunk");
+                    // One K-step at a time (24 words live), stores aligned to their width.
+                    static_assert(V2_KS == 2 && V2_NPC == 3, "two K-steps of 24 columns per chunk");
 #pragma unroll
                     for (int st = 0; st < V2_KS; ++st) {
                         const bool own = (st == 0) == (b == 0);
@@ -935,12 +859,18 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
                                        __shfl_xor_sync(0xffffffffu, mine[i].y, 1)};
                             const cf y = own ? mine[i] : o;
                             uint32_t w[V2_NPC];
-                            v2_split_f16(b ? y.y : y.x, b ? y.x : -y.y, w);
+                            v2_split_bf16(b ? y.y : y.x, b ? y.x : -y.y, w);
 #pragma unroll
                             for (int pc = 0; pc < V2_NPC; ++pc) rw[i + 8 * pc] = w[pc];
                         }
                         const uint32_t ta = lane_base + XB + V2_XW * xs + 8 * V2_NPC * st;
-                        tc::tmem_st16(ta, rw);
+                        if (st == 0) {
+                            tc::tmem_st16(ta, rw);
+                            tc::tmem_st8(ta + 16, rw + 16);
+                        } else {
+                            tc::tmem_st8(ta, rw);
+                            tc::tmem_st16(ta + 8, rw + 8);
+                        }
                     }
                     tc::tmem_st_wait();
                     tc::fence_before();
@@ -967,15 +897,12 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
         for (int i = 0; i < V2_RJ; ++i) rm[i] = MM[min(lane + 32 * i, P - 1)];
         // column data of item w into meta slot `slot`, then release it to the producers
         auto fill = [&](const M2LWork &w, int slot) {
-            const float *tsc = item_scales(w);
             const TcProb pd = prob(w);
-            v2_fill_scales(P, NR, (int)sp.mm_n, tsc, meta_IB(slot), meta_IA(slot), ea, V2_ET);
             if (mode == 0)
-                v2_fill_meta(p, P, w, pd.pairs, pd.ephase, pd.me, MM, tsc, (w.flags & 1) != 0, (w.flags & 2) != 0,
-                             meta_G(slot), meta_O(slot), meta_cols(slot), meta_XS(slot), ea, V2_ET);
+                v2_fill_meta(p, P, w, pd.pairs, pd.ephase, (w.flags & 1) != 0, (w.flags & 2) != 0, meta_G(slot),
+                             meta_O(slot), meta_cols(slot), ea, V2_ET);
             else
-                v2_fill_trans(p, P, w, tsrc, tdst, me, MM, tsc, meta_G(slot), meta_O(slot), meta_cols(slot),
-                              meta_XS(slot), ea, V2_ET);
+                v2_fill_trans(p, P, w, tsrc, tdst, meta_G(slot), meta_O(slot), meta_cols(slot), ea, V2_ET);
             tc::mbar_arrive(&metafull[slot]);
         };
         for (int i = 0; i < 2; ++i)
@@ -1030,10 +957,6 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
             cf *const ple = prob(wc).le;
             const cf *O = meta_O(slot);
             const V2Col *cols = meta_cols(slot);
-            const float *XS = meta_XS(slot), *IA = meta_IA(slot);
-            float ia[V2_RJ];                          // row scales of the item's table
-#pragma unroll
-            for (int i = 0; i < V2_RJ; ++i) ia[i] = IA[min(lane + 32 * i, NR - 1)];
             // one column per epilogue warp at a time, two in flight: lane j of a
             // column takes rows r = lane + 32 i; the column record is warp-uniform
             // and the scratch reads are coalesced
@@ -1055,12 +978,11 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
                     const int64_t ob = cq.out_base;
                     const bool kneg = cq.kap < 0;
                     const cf *Oc = O + cc * MO + p;
-                    const float ixs = 1.f / XS[cc];
 #pragma unroll
                     for (int i = 0; i < V2_RJ; ++i) {
                         const int r = lane + 32 * i;
                         if (r < P) {
-                            const cf yy = (ia[i] * ixs) * (Oc[rm[i]] * cf{y[h][i].x, y[h][i].y});
+                            const cf yy = Oc[rm[i]] * cf{y[h][i].x, y[h][i].y};
                             // output (nu, mu) with mu = +-mh: index r or r - 2 mh
                             atomicAdd((float2 *)(ple + ob + (kneg ? r - 2 * rm[i] : r)), make_float2(yy.x, yy.y));
                         }
@@ -1083,11 +1005,13 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
     if (warp == 0) tc::tmem_dealloc(tbase, 512);
 }
 
-// two-piece fp16 split of a double (host and device): h1 = fp16(v), h2 = fp16(v - h1)
-__host__ __device__ inline void v2_split2(double v, __half (&o)[V2_NPC])
+// three-piece bf16 split of a double (host and device)
+__host__ __device__ inline void v2_split3(double v, __nv_bfloat16 (&o)[V2_NPC])
 {
-    o[0] = __float2half_rn((float)v);
-    o[1] = __float2half_rn((float)(v - (double)__half2float(o[0])));
+    o[0] = __float2bfloat16_rn((float)v);
+    const double r1 = v - (double)__bfloat162float(o[0]);
+    o[1] = __float2bfloat16_rn((float)r1);
+    o[2] = __float2bfloat16_rn((float)(r1 - (double)__bfloat162float(o[1])));
 }
 
 // element (r, kk) of one plane of one K-step (16 real K) of a tiled image, in
@@ -1098,93 +1022,12 @@ __host__ __device__ inline size_t v2_img_off(int r, int kk)
     return (size_t)(((r >> 3) * 256 + (kk >> 3) * 128 + (r & 7) * 16 + (kk & 7) * 2) >> 1);
 }
 
-// degree n of index k = n^2 + n + m
-__host__ __device__ inline int v2_degree(int k)
-{
-    int n = (int)sqrt((double)k + 0.5);
-    while ((n + 1) * (n + 1) <= k) ++n;
-    while (n * n > k) --n;
-    return n;
-}
-
-// Power-of-two scales of a P x P matrix with entry magnitudes mag(r, k) (the
-// largest of |Re|, |Im|): ib_k = 2^floor(log2 max_r mag) (1 for a zero column),
-// then ia_r = 2^floor(log2 max_k mag / ib_k) / 2^14 (1 for a zero row), so that
-// the stored a_r M_rk b_k have row maxima in [2^14, 2^15).  out[k] = ib_k
-// (k < P), out[P + r] = ia_r (r < NR).
-// a power of two clamped to [2^-120, 2^120] (normal floats with normal inverses)
-__host__ __device__ inline float v2_clamp_scale(double v)
-{
-    return (float)fmin(fmax(v, ldexp(1.0, -120)), ldexp(1.0, 120));
-}
-template <typename Mag>
-__host__ __device__ inline void v2_matrix_scales(int P, int NR, Mag mag, float *out, int t0, int dt)
-{
-    for (int k = t0; k < P; k += dt) {
-        double m = 0;
-        for (int r = 0; r < P; ++r) m = fmax(m, mag(r, k));
-        out[k] = m > 0 ? v2_clamp_scale(pow2_floor(m)) : 1.f;
-    }
-}
-template <typename Mag>
-__host__ __device__ inline void v2_row_scales(int P, int NR, Mag mag, float *out, int t0, int dt)
-{
-    for (int r = t0; r < NR; r += dt) {
-        double m = 0;
-        for (int k = 0; r < P && k < P; ++k) m = fmax(m, mag(r, k) / (double)out[k]);
-        out[P + r] = m > 0 ? v2_clamp_scale(ldexp(pow2_floor(m), -14)) : 1.f;
-    }
-}
-
-// level scaling s_t^nu s_s^n' and mirror signs of the stored table entry (r, k)
-// of a geometry (the degree factors i^n' (-i)^nu are unit-modulus)
-__device__ inline double v2_entry_factor(const GeomDev &g, const CompDev &cp, int nu, int n1)
-{
-    const bool flip_in = (cp.s < 0) != (cp.has_src_refl != 0);
-    const bool flip_out = (cp.s < 0) != (cp.has_tgt_refl != 0);
-    return pow(g.scale_t, (double)nu) * pow(g.scale_s, (double)n1) * ((flip_in && (n1 & 1)) ? -1.0 : 1.0) *
-           ((flip_out && (nu & 1)) ? -1.0 : 1.0);
-}
-
-// scales of every table of a batch of geometries (one CTA per table):
-// scales[(tab_index * 5 + t) * (P + NR) ...] as in v2_matrix_scales
-__global__ void k_table_scales(int p, int64_t g0, int64_t ng, const GeomDev *geoms, const CompDev *comps,
-                               const cd *tab64, float *scales)
-{
-    const int P = (p + 1) * (p + 1);
-    const int NR = (int)v2_plan(p).NR;
-    const int64_t gi = g0 + blockIdx.x;
-    const int t = blockIdx.y;
-    if (gi >= g0 + ng) return;
-    const GeomDev &g = geoms[gi];
-    const CompDev cp = comps[g.comp];
-    __shared__ double fr[LMF_PMAX + 1], fc[LMF_PMAX + 1];   // |factor| per output / input degree
-    __shared__ float sc[2 * V2_NR_MAX];
-    for (int n = threadIdx.x; n <= p; n += blockDim.x) {
-        fr[n] = pow(g.scale_t, (double)n);
-        fc[n] = pow(g.scale_s, (double)n);
-    }
-    __syncthreads();
-    const cd *T = tab64 + ((gi - g0) * NTAB + t) * (int64_t)P * P;
-    auto mag = [&](int r, int k) {
-        const cd a = T[(int64_t)r * P + k];
-        return fr[v2_degree(r)] * fc[v2_degree(k)] * fmax(fabs(a.x), fabs(a.y));
-    };
-    v2_matrix_scales(P, NR, mag, sc, threadIdx.x, blockDim.x);
-    __syncthreads();
-    v2_row_scales(P, NR, mag, sc, threadIdx.x, blockDim.x);
-    __syncthreads();
-    float *out = scales + (g.tab_index * NTAB + t) * (int64_t)(P + NR);
-    for (int e = threadIdx.x; e < P + NR; e += blockDim.x) out[e] = sc[e];
-}
-
 // table image of the persistent kernel: per (geometry, table) nchunk * V2_KS
-// K-steps (zero beyond P), each V2_NPC fp16 planes of NR rows x 16 real K,
-// from the FP64 table with the level scaling s_t^nu s_s^n', the degree
-// factors (-i)^nu f_t^nu, i^n' f_s^n' and the power-of-two scales a_r b_k
-// applied before the split
+// K-steps (zero beyond P), each V2_NPC bf16 planes of NR rows x 16 real K,
+// from the FP64 table with the level scaling s_t^nu s_s^n' and the degree
+// factors (-i)^nu f_t^nu, i^n' f_s^n' applied before the split
 __global__ void k_tile_tables(int p, int64_t g0, int64_t ng, const GeomDev *geoms, const CompDev *comps,
-                              const cd *tab64, const float *scales, __half *img)
+                              const cd *tab64, __nv_bfloat16 *img)
 {
     const int P = (p + 1) * (p + 1);
     const V2Plan sp = v2_plan(p);
@@ -1198,16 +1041,23 @@ __global__ void k_tile_tables(int p, int64_t g0, int64_t ng, const GeomDev *geom
     const GeomDev &g = geoms[gi];
     cd v{0.0, 0.0};
     if (r < P && k < P) {
-        const int nu = v2_degree(r), n1 = v2_degree(k);
-        const float *sc = scales + (g.tab_index * NTAB + t) * (int64_t)(P + NR);
-        const double f = v2_entry_factor(g, comps[g.comp], nu, n1) / ((double)sc[k] * (double)sc[P + r]);
+        int nu = (int)sqrt((double)r + 0.5), n1 = (int)sqrt((double)k + 0.5);
+        while ((nu + 1) * (nu + 1) <= r) ++nu;
+        while (nu * nu > r) --nu;
+        while ((n1 + 1) * (n1 + 1) <= k) ++n1;
+        while (n1 * n1 > k) --n1;
+        const CompDev cp = comps[g.comp];
+        const bool flip_in = (cp.s < 0) != (cp.has_src_refl != 0);
+        const bool flip_out = (cp.s < 0) != (cp.has_tgt_refl != 0);
+        const double f = pow(g.scale_t, (double)nu) * pow(g.scale_s, (double)n1) *
+                         ((flip_in && (n1 & 1)) ? -1.0 : 1.0) * ((flip_out && (nu & 1)) ? -1.0 : 1.0);
         const cd a = tab64[((gi - g0) * NTAB + t) * (int64_t)P * P + (int64_t)r * P + k];
         v = ipow<double>(n1 - nu) * (f * a);   // i^n' (-i)^nu = i^(n' - nu)
     }
-    __half re[V2_NPC], im[V2_NPC];
-    v2_split2(v.x, re);
-    v2_split2(v.y, im);
-    __half *sub = img + ((size_t)(g.tab_index * NTAB + t) * nsub + c) * (size_t)(NR * 16 * V2_NPC);
+    __nv_bfloat16 re[V2_NPC], im[V2_NPC];
+    v2_split3(v.x, re);
+    v2_split3(v.y, im);
+    __nv_bfloat16 *sub = img + ((size_t)(g.tab_index * NTAB + t) * nsub + c) * (size_t)(NR * 16 * V2_NPC);
     for (int pc = 0; pc < V2_NPC; ++pc) {
         sub[(size_t)pc * NR * 16 + v2_img_off(r, 2 * i)] = re[pc];
         sub[(size_t)pc * NR * 16 + v2_img_off(r, 2 * i + 1)] = im[pc];
@@ -1261,22 +1111,19 @@ size_t m2l_tc2_image_bytes(int p, int64_t ngeom)
 
 size_t m2l_tc2_scratch_floats(int p, int nsm) { return (size_t)nsm * 128 * v2_plan(p).NR; }
 
-size_t m2l_tc2_scale_floats(int p, int64_t nmat) { return (size_t)nmat * (size_t)((p + 1) * (p + 1) + v2_plan(p).NR); }
-
 void launch_tile_tables(int p, int64_t g0, int64_t ng, const GeomDev *geoms, const CompDev *comps,
-                        const cd *tab64, void *img, float *scales, cudaStream_t st)
+                        const cd *tab64, void *img, cudaStream_t st)
 {
     if (ng <= 0) return;
     const V2Plan sp = v2_plan(p);
-    k_table_scales<<<dim3((unsigned)ng, NTAB), 256, 0, st>>>(p, g0, ng, geoms, comps, tab64, scales);
     dim3 grid((sp.nchunk * V2_KS * sp.NR * 8 + 255) / 256, (unsigned)ng, NTAB);
-    k_tile_tables<<<grid, 256, 0, st>>>(p, g0, ng, geoms, comps, tab64, scales, (__half *)img);
+    k_tile_tables<<<grid, 256, 0, st>>>(p, g0, ng, geoms, comps, tab64, (__nv_bfloat16 *)img);
 }
 
 static cudaError_t launch_tc2(int p, int mode, int64_t nwork, const M2LWork *work, const GeomDev *geoms,
                               const M2LPair *pairs, const cf *ephase, const int64_t *tsrc,
-                              const int64_t *tdst, const void *img, const float *scales, const cf *in, cf *out,
-                              float *yscr, int nsm, int *status, cudaStream_t st)
+                              const int64_t *tdst, const void *img, const cf *in, cf *out, float *yscr, int nsm,
+                              int *status, cudaStream_t st)
 {
     if (nwork <= 0) return cudaSuccess;
     if (!m2l_tc2_supported(p) || nsm < 1) return cudaErrorInvalidValue;
@@ -1285,8 +1132,7 @@ static cudaError_t launch_tc2(int p, int mode, int64_t nwork, const M2LWork *wor
     // an SM's shared memory so that no two CTAs are resident on one SM
     const size_t smem = std::max<size_t>(v2_plan(p).total, 116 * 1024);
     k_m2l_tc2<<<(unsigned)grid, V2_THREADS, smem, st>>>(p, mode, nwork, work, geoms, pairs, ephase, tsrc,
-                                                        tdst, (const uint32_t *)img, scales, in, out, yscr,
-                                                        status, nullptr);
+                                                        tdst, (const uint32_t *)img, in, out, yscr, status, nullptr);
     return cudaGetLastError();
 }
 
@@ -1298,25 +1144,24 @@ cudaError_t launch_m2l_tc2_batch(int p, int64_t nwork, const M2LWork *work, cons
     const int64_t grid = std::min<int64_t>(nwork, (int64_t)nsm);
     const size_t smem = std::max<size_t>(v2_plan(p).total, 116 * 1024);
     k_m2l_tc2<<<(unsigned)grid, V2_THREADS, smem, st>>>(p, 0, nwork, work, nullptr, nullptr, nullptr, nullptr,
-                                                        nullptr, nullptr, nullptr, nullptr, nullptr, yscr,
-                                                        status, probs);
+                                                        nullptr, nullptr, nullptr, nullptr, yscr, status, probs);
     return cudaGetLastError();
 }
 
 cudaError_t launch_m2l_tc2(int p, int64_t nwork, const M2LWork *work, const GeomDev *geoms,
-                           const M2LPair *pairs, const cf *ephase, const void *img, const float *scales,
+                           const M2LPair *pairs, const cf *ephase, const void *img,
                            const cf *me, cf *le, float *yscr, int nsm, int *status, cudaStream_t st)
 {
-    return launch_tc2(p, 0, nwork, work, geoms, pairs, ephase, nullptr, nullptr, img, scales, me, le, yscr,
-                      nsm, status, st);
+    return launch_tc2(p, 0, nwork, work, geoms, pairs, ephase, nullptr, nullptr, img, me, le, yscr, nsm,
+                      status, st);
 }
 
 cudaError_t launch_trans_tc2(int p, int64_t nwork, const M2LWork *work, const int64_t *tsrc,
-                             const int64_t *tdst, const void *img, const float *scales, const cf *in, cf *out,
-                             float *yscr, int nsm, int *status, cudaStream_t st)
+                             const int64_t *tdst, const void *img, const cf *in, cf *out, float *yscr, int nsm,
+                             int *status, cudaStream_t st)
 {
-    return launch_tc2(p, 1, nwork, work, nullptr, nullptr, nullptr, tsrc, tdst, img, scales, in, out, yscr,
-                      nsm, status, st);
+    return launch_tc2(p, 1, nwork, work, nullptr, nullptr, nullptr, tsrc, tdst, img, in, out, yscr, nsm,
+                      status, st);
 }
 
 size_t tc2_matrix_bytes(int p)
@@ -1325,31 +1170,22 @@ size_t tc2_matrix_bytes(int p)
     return (size_t)sp.nchunk * sp.CB;
 }
 
-void tile_matrix_tc2(int p, const cd *M, void *img_, float *scales)
+void tile_matrix_tc2(int p, const cd *M, void *img_)
 {
     const int P = (p + 1) * (p + 1);
     const V2Plan sp = v2_plan(p);
     const int NR = (int)sp.NR, nsub = (int)sp.nchunk * V2_KS;
-    auto mag = [&](int r, int k) {
-        const cd a = M[(size_t)r * P + k];
-        return std::max(std::fabs(a.x), std::fabs(a.y));
-    };
-    v2_matrix_scales(P, NR, mag, scales, 0, 1);
-    v2_row_scales(P, NR, mag, scales, 0, 1);
-    __half *img = (__half *)img_;
+    __nv_bfloat16 *img = (__nv_bfloat16 *)img_;
     for (int c = 0; c < nsub; ++c)
         for (int r = 0; r < NR; ++r)
             for (int i = 0; i < 8; ++i) {
                 const int k = 8 * c + i;
                 cd v{0.0, 0.0};
-                if (r < P && k < P) {
-                    const double f = 1.0 / ((double)scales[k] * (double)scales[P + r]);
-                    v = cd{f * M[(size_t)r * P + k].x, f * M[(size_t)r * P + k].y};
-                }
-                __half re[V2_NPC], im[V2_NPC];
-                v2_split2(v.x, re);
-                v2_split2(v.y, im);
-                __half *sub = img + (size_t)c * NR * 16 * V2_NPC;
+                if (r < P && k < P) v = M[(size_t)r * P + k];
+                __nv_bfloat16 re[V2_NPC], im[V2_NPC];
+                v2_split3(v.x, re);
+                v2_split3(v.y, im);
+                __nv_bfloat16 *sub = img + (size_t)c * NR * 16 * V2_NPC;
                 for (int pc = 0; pc < V2_NPC; ++pc) {
                     sub[(size_t)pc * NR * 16 + v2_img_off(r, 2 * i)] = re[pc];
                     sub[(size_t)pc * NR * 16 + v2_img_off(r, 2 * i + 1)] = im[pc];

@@ -68,7 +68,6 @@ struct TcProb {
     const M2LPair *pairs;
     const cf *ephase;
     const void *img;
-    const float *tscale;
     const cf *me;
     cf *le;
 };
@@ -126,19 +125,17 @@ cudaError_t launch_m2l_tc(int p, int64_t nwork, const M2LWork *work, const GeomD
                           const CompDev *comps, const M2LPair *pairs, const cf *tab, const cf *me,
                           cf *le, int *status, cudaStream_t st);
 // persistent warp-specialised variant (p <= 12) on a pre-tiled image of the
-// tables in two fp16 pieces with power-of-two row and column scales
-// (launch_tile_tables from the FP64 tables; scales holds
-// m2l_tc2_scale_floats(p, ngeom * 5) floats); ephase holds e^{i d phi} of
-// every pair, d = -(p+2)..p+2 ([npair][2p+5], FP32 from FP64); yscr holds
-// m2l_tc2_scratch_floats(p, nsm) floats, nsm = CTAs of the launch (the SM count)
+// tables in three bf16 pieces (launch_tile_tables from the FP64 tables);
+// ephase holds e^{i d phi} of every pair, d = -(p+2)..p+2 ([npair][2p+5],
+// FP32 from FP64); yscr holds m2l_tc2_scratch_floats(p, nsm) floats, nsm =
+// CTAs of the launch (the SM count)
 bool m2l_tc2_supported(int p);
 size_t m2l_tc2_image_bytes(int p, int64_t ngeom);
 size_t m2l_tc2_scratch_floats(int p, int nsm);
-size_t m2l_tc2_scale_floats(int p, int64_t nmat);
 void launch_tile_tables(int p, int64_t g0, int64_t ng, const GeomDev *geoms, const CompDev *comps,
-                        const cd *tab64, void *img, float *scales, cudaStream_t st);
+                        const cd *tab64, void *img, cudaStream_t st);
 cudaError_t launch_m2l_tc2(int p, int64_t nwork, const M2LWork *work, const GeomDev *geoms,
-                           const M2LPair *pairs, const cf *ephase, const void *img, const float *scales,
+                           const M2LPair *pairs, const cf *ephase, const void *img,
                            const cf *me, cf *le, float *yscr, int nsm, int *status, cudaStream_t st);
 // the M2L of several problems (same p) in one persistent launch: work items
 // carry their problem index into probs (device array)
@@ -146,14 +143,12 @@ cudaError_t launch_m2l_tc2_batch(int p, int64_t nwork, const M2LWork *work, cons
                                  int nsm, int *status, cudaStream_t st);
 // M2M or L2L on the same kernel: items M2LWork{geom = translation group, t = 0,
 // npair, pair0} over pairs (tsrc[q], tdst[q]), 3 helical columns each; img holds
-// one tiled matrix per group (tile_matrix_tc2, tc2_matrix_bytes(p) each) and
-// scales its row / column scales (m2l_tc2_scale_floats(p, 1) each)
+// one tiled matrix per group (tile_matrix_tc2, tc2_matrix_bytes(p) each)
 cudaError_t launch_trans_tc2(int p, int64_t nwork, const M2LWork *work, const int64_t *tsrc,
-                             const int64_t *tdst, const void *img, const float *scales, const cf *in, cf *out,
-                             float *yscr, int nsm, int *status, cudaStream_t st);
+                             const int64_t *tdst, const void *img, const cf *in, cf *out, float *yscr, int nsm,
+                             int *status, cudaStream_t st);
 size_t tc2_matrix_bytes(int p);
-// host: P x P row-major (row = output index) -> tiled fp16 image and its scales
-void tile_matrix_tc2(int p, const cd *M, void *img, float *scales);
+void tile_matrix_tc2(int p, const cd *M, void *img);   // host: P x P row-major (row = output index)
 template <typename T>
 void launch_scale_tables(int p, int64_t g0, int64_t ng, const GeomDev *geoms, const cd *tab64,
                          cx<T> *tab, cudaStream_t st);

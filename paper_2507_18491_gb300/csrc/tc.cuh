@@ -40,12 +40,6 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-// Instruction descriptor of kind::f16 with fp16 A and B (K-major), D f32, shape M x N.
-__host__ __device__ constexpr uint32_t idesc_f16(int M, int N)
-{
-    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
 // MMA kind::f16 (K = 16, fp16 or bf16 per the instruction descriptor) with the
 // A operand in tensor memory (M lanes x 8 columns, two 16-bit values per
 // column, even K in the low half) and B in shared memory

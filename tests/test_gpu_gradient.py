@@ -61,16 +61,19 @@ def test_gradient_against_finite_differences_of_the_fmm():
 
 
 def test_gradient_directional_derivative_three_layer_32768():
-    """The adjoint configuration's size: N = 32768, p = 10, all coordinates
-    displaced at once along a random direction."""
+    """The adjoint configuration's size: N = 32768, p = 10; 32 random
+    coordinates displaced at once along a random direction (h = 1e-6; the
+    tree, lists and quadrature rules are those of the undisplaced points)."""
     w, J, Eref, kw, gJ, gx, adj, st = _setup(32768, 10, 4)
     rng = np.random.default_rng(3)
-    v = rng.standard_normal(w.xyz.shape)
+    v = np.zeros(w.xyz.shape)
+    idx = rng.choice(w.xyz.size, 32, replace=False)
+    v.flat[idx] = rng.standard_normal(32)
     h = 1e-6
     fd = (_f(w, w.xyz + h * v, J, Eref, kw) - _f(w, w.xyz - h * v, J, Eref, kw)) / (2 * h)
     an = float(np.sum(gx * v))
     print("directional derivative: analytic %.9e  central differences %.9e" % (an, fd))
-    assert abs(an - fd) < 1e-5 * np.linalg.norm(gx) * np.linalg.norm(v)
+    assert abs(an - fd) < 1e-6 * abs(an)
 
 
 def test_autograd_function_matches_vjp():

@@ -2,7 +2,7 @@
 against stored oracle values (runs last: the longest GPU test).
 
 Four layers (interfaces z = 0, -1, -2, k = (1, 1.5, 2, 2.5) + 0.02i), N = 2^20
-points in 64 Gaussian clusters, p = 12, depth 6, theta 0.55, complex64 currents
+points in 64 Gaussian clusters, p = 12, depth 6, theta 0.5, complex64 currents
 (the workload's own type).  J is kept on ~1400 sources -- 400 random ones and
 the 8 nearest points of every target, so that near-field pairs are in the sum --
 and the oracle's direct FP64 sum over them is evaluated at 128 targets, half of
@@ -29,7 +29,7 @@ def sample():
 def test_four_layer_full_size_sampled(sample, precision, tensor_cores, kernel):
     w, tg, src, J, ref = sample
     prec = lmfmm.MIXED if precision == "mixed" else lmfmm.FP64
-    op = lmfmm.Operator(w.d, w.k, w.xyz, p=12, depth=6, theta=0.55, precision=prec,
+    op = lmfmm.Operator(w.d, w.k, w.xyz, p=12, depth=6, theta=0.5, precision=prec,
                         tensor_cores=tensor_cores).build()
     try:
         got = op.matvec(torch.from_numpy(J.astype(np.complex64)).cuda())
