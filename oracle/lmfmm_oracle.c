@@ -408,6 +408,10 @@ typedef struct {
     long nfev;
     cplx *buf;      /* nv */
     cplx *kr15;     /* 15*nv */
+    /* per-component error control (NULL: one tolerance for all components,
+     * relative to the largest): the error estimate and L1 magnitude of every
+     * component from the last gk15 call, and each component's L1 scale */
+    double *cerr, *cmag, *cscale;
 } quad_ws;
 
 /* Gauss-Kronrod 7/15 on the straight segment [z0, z1]; returns the error
@@ -440,6 +444,7 @@ static double gk15(quad_ws *w, cplx z0, cplx z1, cplx *K, double *l1)
         if (e > err) err = e;
         double a = A[v] * cabs(h);
         if (a > s1) s1 = a;
+        if (w->cerr) { w->cerr[v] = e; w->cmag[v] = a; }
     }
     free(A);
     if (l1) *l1 = s1;
@@ -466,6 +471,30 @@ static void adapt(quad_ws *w, cplx z0, cplx z1, double tol, int depth, cplx *acc
     cplx zm = 0.5 * (z0 + z1);
     adapt(w, z0, zm, 0.5 * tol, depth + 1, acc, NULL, 0, 0);
     adapt(w, zm, z1, 0.5 * tol, depth + 1, acc, NULL, 0, 0);
+}
+
+/* per-component form of adapt: every component must meet its own share of
+ * the tolerance, frac times its L1 scale over the whole path (or the
+ * round-off floor of its own magnitude on the segment) */
+static void adapt_pc(quad_ws *w, cplx z0, cplx z1, double frac, int depth, cplx *acc)
+{
+    cplx *K = (cplx *)malloc(sizeof(cplx) * w->nv);
+    gk15(w, z0, z1, K, NULL);
+    int ok = depth >= 24;
+    if (!ok) {
+        ok = 1;
+        for (int v = 0; v < w->nv && ok; ++v)
+            if (w->cerr[v] > frac * w->cscale[v] && w->cerr[v] > 50.0 * 2.2e-16 * w->cmag[v]) ok = 0;
+    }
+    if (ok) {
+        for (int v = 0; v < w->nv; ++v) acc[v] += K[v];
+        free(K);
+        return;
+    }
+    free(K);
+    cplx zm = 0.5 * (z0 + z1);
+    adapt_pc(w, z0, zm, 0.5 * frac, depth + 1, acc);
+    adapt_pc(w, zm, z1, 0.5 * frac, depth + 1, acc);
 }
 
 /*
@@ -510,6 +539,18 @@ static void integrate_path(quad_ws *w, const path_spec *ps, cplx *res)
     for (int j = 0; j < np; ++j) {
         err[2 * j] = gk15(w, pz0[j], pz1[j], K + (size_t)j * nv, &err[2 * j + 1]);
         scale += err[2 * j + 1];
+    }
+    if (w->cscale) {
+        /* per component: the scale is the component's own L1 integral */
+        for (int v = 0; v < nv; ++v) w->cscale[v] = 0.0;
+        for (int j = 0; j < np; ++j) {
+            gk15(w, pz0[j], pz1[j], K, NULL);
+            for (int v = 0; v < nv; ++v) w->cscale[v] += w->cmag[v];
+        }
+        for (int j = 0; j < np; ++j) adapt_pc(w, pz0[j], pz1[j], ps->rtol / sqrt((double)np), 0, acc);
+        free(pz0); free(pz1); free(K); free(G); free(err);
+        w->kr15 = NULL;
+        return;
     }
     if (scale == 0.0) scale = 1e-300;
     double tol = ps->rtol * scale;
@@ -947,9 +988,13 @@ int or_m2l_table(int L, const double *d, const double *kri, int l, int lp, int t
     if (D <= 0) return -1;
     cplx *buf = (cplx *)malloc(sizeof(cplx) * P * P);
     cplx *res = (cplx *)malloc(sizeof(cplx) * P * P);
-    quad_ws w = {m2l_integrand, &c, P * P, 0, buf, NULL};
+    /* every entry is its own Sommerfeld integral: each meets rtol relative to
+     * its own magnitude (entries of low and high degree differ by many orders) */
+    double *ce = (double *)malloc(sizeof(double) * 3 * P * P);
+    quad_ws w = {m2l_integrand, &c, P * P, 0, buf, NULL, ce, ce + P * P, ce + 2 * P * P};
     path_spec ps = {medium_a(&m), 0.4, D, rho, rtol, 2 * p + 3, 0.0};
     integrate_path(&w, &ps, res);
+    free(ce);
     for (int i = 0; i < P * P; ++i) { out[2 * i] = creal(res[i]); out[2 * i + 1] = cimag(res[i]); }
     free(buf); free(res);
     return 0;

@@ -121,9 +121,10 @@ def test_m2l_tables_p12_match_oracle():
                             continue
                         worst = max(worst, np.max(np.abs(got[t][np.ix_(rs, cs)] - r)) / sc)
             print("geometry %d: worst blockwise relative difference %.3e" % (gi, worst))
-            # the fixed composite Gauss-Legendre rule (16 nodes per Gamma_1 panel) leaves a
-            # few 1e-9 in the degree-12 blocks; 1e-8 is a sixth of the mixed form's
-            # rounding of the same entries (2^-24) and 1e-2 of the 1e-6 target
+            # the fixed composite Gauss-Legendre rule (16 nodes per Gamma_1 panel) agrees
+            # with the oracle's per-entry adaptive integrals to a few 1e-10; 1e-8 is a
+            # sixth of the mixed form's rounding of the same entries (2^-24) and 1e-2 of
+            # the 1e-6 target
             assert worst < 1e-8
     finally:
         lmfmm.destroy(ctx)

@@ -134,3 +134,20 @@ def test_same_layer_tables_depend_on_the_vertical_offset_only():
     c = O.m2l_table(d, k, 0, 1, 1, 1, 1, 0, p, rho, 0.45, -0.5, rtol=1e-13)
     e = O.m2l_table(d, k, 0, 1, 1, 1, 1, 0, p, rho, 0.60, -0.35, rtol=1e-13)
     assert np.max(np.abs(c - e)) > 1e-3 * np.max(np.abs(c))
+
+
+def test_table_entries_do_not_depend_on_the_truncation():
+    """Each entry I-hat[(nu, mu), (n', m')] of eq. onedimensionintegral is its own
+    Sommerfeld integral: the entries of degrees <= 2 computed in a p = 2 table
+    and in a p = 9 table must agree entry by entry, although the p = 9 table
+    also holds entries larger by many orders (the high-degree Legendre products
+    grow like k_rho^(n + n')).  A tolerance shared by all entries of a table
+    fails this for the small low-degree entries."""
+    d, k = np.array([0.0, -1.0, -2.0]), np.array([1.0, 1.5, 2.0, 2.5]) + 0.02j
+    # transmission from layer 2 up into layer 1, horizontal offset = vertical distance
+    args = (d, k, 2, 1, 1, 1, 5, 0)
+    small = O.m2l_table(*args, 2, 0.45, -1.2, -0.75, rtol=1e-12)
+    big = O.m2l_table(*args, 9, 0.45, -1.2, -0.75, rtol=1e-12)[:9, :9]
+    assert np.max(np.abs(big) / np.max(np.abs(small))) < 1e3
+    rel = np.abs(big - small) / np.abs(small)
+    assert np.max(rel) < 1e-10, np.max(rel)
