@@ -26,6 +26,8 @@ struct DevState {
     BoxDev *boxes = nullptr;
     int64_t *leaves = nullptr;
     int64_t nleaves = 0;
+    int *pt_box = nullptr;           // leaf box of every sorted point (mixed form)
+    bool leaf_fast = false;          // mixed form, p <= 15: L2P of k_leaf.cu
     cd *qh = nullptr, *ph = nullptr; // helical, sorted [N][3]
     void *me = nullptr, *le = nullptr; // [nbox][3][P], complex T (scaled)
     CompDev *comps = nullptr;
@@ -354,7 +356,8 @@ lmfmm_status lmfmm_create(lmfmm_ctx **out, const lmfmm_params *prm, int device)
         g_err = std::string("cudaSetDevice: ") + cudaGetErrorString(e);
         return LMFMM_ERR_CUDA;
     }
-    if ((e = configure_fmm_kernels()) != cudaSuccess || (e = configure_tab_kernels()) != cudaSuccess) {
+    if ((e = configure_fmm_kernels()) != cudaSuccess || (e = configure_tab_kernels()) != cudaSuccess ||
+        (e = configure_leaf_fast()) != cudaSuccess) {
         g_err = std::string("kernel configuration: ") + cudaGetErrorString(e);
         return LMFMM_ERR_CUDA;
     }
@@ -483,6 +486,15 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
     TRY(dupload(ctx, &d->boxes, hb));
     TRY(dupload(ctx, &d->leaves, leaves));
     d->nleaves = (int64_t)leaves.size();
+    if (ctx->prm.precision == LMFMM_MIXED && leaf_fast_supported(p)) {
+        std::vector<int> ptb(N > 0 ? N : 1, 0);
+        for (int64_t li : leaves) {
+            const Box &b = ctx->boxes[li];
+            for (int64_t q = b.p0; q < b.p1; ++q) ptb[q] = (int)li;
+        }
+        TRY(dupload(ctx, &d->pt_box, ptb));
+        d->leaf_fast = true;
+    }
     TRY(dalloc(ctx, &d->qh, 3 * N));
     TRY(dalloc(ctx, &d->ph, 3 * N));
     const bool f32 = ctx->prm.precision == LMFMM_MIXED;
@@ -802,6 +814,31 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
 }
 
 extern "C++" {
+// P2M / L2P at the leaves (per-leaf kernels; the mixed form's L2P runs one
+// thread per point, k_leaf.cu, where it applies).  l2p_basis / p2m_basis: the
+// transposes.
+template <typename T>
+static void leaf_p2m(lmfmm_ctx *ctx, const cd *in, cx<T> *out, bool l2p_basis, cudaStream_t st)
+{
+    DevState *d = DS(ctx);
+    launch_p2m<T>(ctx->prm.p, d->nleaves, d->leaves, d->boxes, d->xyz, in, ctx->med, d->lscale, out, st, l2p_basis);
+}
+
+template <typename T>
+static void leaf_l2p(lmfmm_ctx *ctx, const cx<T> *in, cd *out, bool p2m_basis, cudaStream_t st)
+{
+    DevState *d = DS(ctx);
+    const int p = ctx->prm.p;
+    if constexpr (std::is_same<T, float>::value) {
+        if (d->leaf_fast) {
+            launch_l2p_fast(p, ctx->N, d->pt_box, d->boxes, d->xyz, in, ctx->med, d->lscale, out, p2m_basis,
+                            p2m_basis ? 4.0 * 3.14159265358979323846 : 1.0, false, st);
+            return;
+        }
+    }
+    launch_l2p<T>(p, d->nleaves, d->leaves, d->boxes, d->xyz, in, ctx->med, d->lscale, out, st, p2m_basis, false);
+}
+
 // stages of one matvec, for the batched launch: the upward pass (gather, P2M,
 // M2M), the M2L (own_m2l = false: only the clearing of the local expansions,
 // the M2L itself runs in the batch's merged launch), the downward pass
@@ -824,7 +861,7 @@ static lmfmm_status matvec_t(lmfmm_ctx *ctx, const void *J, int dtype, void *Phi
     nl += N > 0;
     nl += d->nleaves > 0;   // P2M
     CK(cudaMemsetAsync(me, 0, (size_t)nbox * 3 * P * sizeof(cx<T>), st));
-    launch_p2m<T>(p, d->nleaves, d->leaves, d->boxes, d->xyz, d->qh, ctx->med, d->lscale, me, st);
+    leaf_p2m<T>(ctx, d->qh, me, false, st);
     CK(cudaEventRecord(d->ev[1], st));
     for (int lev = ctx->depth; lev >= 1; --lev) {
         if constexpr (std::is_same<T, float>::value) {
@@ -883,7 +920,7 @@ static lmfmm_status matvec_t(lmfmm_ctx *ctx, const void *J, int dtype, void *Phi
         nl += w1 > w0;
     }
     CK(cudaEventRecord(d->ev[4], st));
-    launch_l2p<T>(p, d->nleaves, d->leaves, d->boxes, d->xyz, le, ctx->med, d->lscale, d->ph, st);
+    leaf_l2p<T>(ctx, le, d->ph, false, st);
     CK(cudaEventRecord(d->ev[5], st));
     launch_s2t_apply8(d->n_s2twork, d->s2twork, d->near, d->boxes, d->s2t, d->qh, d->ph, st);
     launch_p2p_free(d->n_frows, d->frows, d->fpairs, d->boxes, d->xyz, ctx->med, d->qh, d->ph, false, st);
@@ -918,7 +955,7 @@ static lmfmm_status matvec_tr_t(lmfmm_ctx *ctx, const void *y, int dtype, void *
     CK(cudaMemsetAsync(d->mvstatus, 0, sizeof(int), st));
     launch_gather_tr(N, d->perm, y, dtype, d->ph, cj, st);   // ph <- S^T y
     CK(cudaMemsetAsync(le, 0, (size_t)nbox * 3 * P * sizeof(cx<T>), st));
-    launch_p2m<T>(p, d->nleaves, d->leaves, d->boxes, d->xyz, d->ph, ctx->med, d->lscale, le, st, true);
+    leaf_p2m<T>(ctx, d->ph, le, true, st);
     nl += (N > 0) + (d->nleaves > 0);
     CK(cudaEventRecord(d->ev[1], st));
     for (int lev = ctx->depth; lev >= 1; --lev) {   // L2L^T: children into parents
@@ -937,7 +974,7 @@ static lmfmm_status matvec_tr_t(lmfmm_ctx *ctx, const void *y, int dtype, void *
         nl += w1 > w0;
     }
     CK(cudaEventRecord(d->ev[4], st));
-    launch_l2p<T>(p, d->nleaves, d->leaves, d->boxes, d->xyz, me, ctx->med, d->lscale, d->qh, st, true, false);
+    leaf_l2p<T>(ctx, me, d->qh, true, st);
     CK(cudaEventRecord(d->ev[5], st));
     launch_s2t_apply8_tr(d->n_s2tworkT, d->s2tworkT, d->near, d->boxes, d->s2t, d->ph, d->qh, st);
     launch_p2p_free(d->n_frowsT, d->frowsT, d->fpairs, d->boxes, d->xyz, ctx->med, d->ph, d->qh, true, st);

@@ -383,10 +383,11 @@ __global__ void __launch_bounds__(NT) k_m2l_tc(int p, int MT, uint32_t tmem_cols
 // output order mu.  Roles (576 threads, one CTA per SM -- the tensor memory
 // holds one CTA's accumulators, so latency is hidden by more warps per role):
 //   warps 0-7   X producers, two groups of four warps (one per tensor-memory
-//               lane quadrant) taking alternate K-chunks: the work item's 64
-//               columns, coefficients prefetched V2_D of the group's chunks
-//               ahead, phase-shifted, split into three bf16 pieces and written
-//               into a V2_SX-slot tensor-memory ring (A operand);
+//               lane quadrant), group g writing K-step g of every chunk: the
+//               work item's 64 columns, coefficients prefetched V2_D chunks
+//               ahead, phase-shifted, split once into three bf16 pieces (the
+//               two rows of a column share the pieces) and written into a
+//               V2_SX-slot tensor-memory ring (A operand);
 //   warps 8-15  epilogue, two warps per lane quadrant taking alternate row
 //               slabs: accumulators -> a per-CTA column-major scratch in global
 //               memory through a per-warp shared tile (L2-resident; tensor
@@ -410,8 +411,8 @@ constexpr int V2_NPC = 3;          // bf16 pieces per value
 constexpr int V2_XW = 8 * V2_NPC * V2_KS;   // tensor-memory columns of an X chunk
 constexpr int V2_SX = 3;           // X ring slots
 constexpr int V2_ST_MAX = 16;      // table ring slots (shared memory)
-constexpr int V2_PG = 2;           // producer groups (alternate chunks)
-constexpr int V2_D = 2;            // chunks of a group prefetched into registers
+constexpr int V2_PG = 2;           // producer groups (one K-step of every chunk each)
+constexpr int V2_D = 3;            // chunks prefetched into registers
 constexpr int V2_NR_MAX = 176;     // table rows padded to 16: 2 NR + V2_SX V2_XW <= 512, p <= 12
 constexpr int V2_PT = 128 * V2_PG; // producer threads
 constexpr int V2_ET = 256;         // epilogue threads
@@ -461,12 +462,6 @@ __device__ __forceinline__ cf lds_cf(uint32_t a)
 {
     cf v;
     asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
-    return v;
-}
-__device__ __forceinline__ uint4 lds_u4(uint32_t a)
-{
-    uint4 v;
-    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
     return v;
 }
 
@@ -639,7 +634,7 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
             tc::mbar_init(&tempty[s], 1);
         }
         for (int s = 0; s < V2_SX; ++s) {
-            tc::mbar_init(&xfull[s], 128);
+            tc::mbar_init(&xfull[s], V2_PT);   // both producer groups (one K-step each)
             tc::mbar_init(&xempty[s], 1);
         }
         tc::mbar_init(accfull, 1);
@@ -753,16 +748,17 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
         }
     } else if (warp < V2_PT / 32) {
         // ------------------------------------------------ X producers
-        const int pg = warp / 4;                       // group: chunks g with g % V2_PG == pg
+        // group pg writes K-step pg of every chunk; the two lanes of a column
+        // (row b = 0: Re, -Im; row b = 1: Im, Re) each load, phase-shift and
+        // split four of the K-step's eight inputs, swap the pieces with the
+        // partner lane and store the K-step's 24 columns of their own row
+        const int pg = warp / 4;
         const int j = tid - pg * 128, cc = j >> 1, b = j & 1;
         const uint32_t lane_base = tbase + ((uint32_t)(32 * (warp & 3)) << 16);
-        uint32_t g0 = 0, li = 0;                       // g0: chunks of this CTA before the item
-        // ring slot of this group's next chunk (global chunks pg, pg + V2_PG, ...),
-        // the parity of its pass and whether the ring has been gone round once
-        int xs = pg % V2_SX;
+        uint32_t li = 0, g = 0;                        // items, chunks of this CTA so far
+        int xs = 0;                                    // ring slot of chunk g
         uint32_t xph = 0;
-        bool xwrapped = false;
-        for (int64_t it = blockIdx.x; it < nwork && !failed; it += gridDim.x, ++li, g0 += nchunk) {
+        for (int64_t it = blockIdx.x; it < nwork && !failed; it += gridDim.x, ++li) {
             const int slot = li & 1;
             cf *G = meta_G(slot);
             V2Col *cols = meta_cols(slot);
@@ -781,108 +777,93 @@ __global__ void __launch_bounds__(V2_THREADS, 1)
             const uint32_t gr = tc::smem_u32(G + q.pp * MO + p);   // input factors of the column
             const cf *pme = prob(w).me;
             const cf *src = pme + q.in_base;
-            // this group's chunks of the item: c = cfirst, cfirst + V2_PG, ...
-            const int cfirst = (int)((pg + V2_PG - (int)(g0 % V2_PG)) % V2_PG);
-            const int nmine = cfirst < nchunk ? (nchunk - cfirst + V2_PG - 1) / V2_PG : 0;
-            constexpr int KC = V2_KC;              // complex inputs per chunk
-            constexpr int KH = KC / 2;             // of which this lane forms KH: kk = b*KH + h
-            float2 pre[V2_D][KH];
-            // input (n', m') reads the expansion at (n', +-m'): index k or k - 2m'.
-            // The two lanes of a column (Re row b = 0, Im row b = 1) each load and
-            // phase-shift half of the chunk's inputs and swap the products.
-            // Loads are unconditional (from a clamped address) so that they stay
-            // in flight until their use V2_D chunks later; the mask is applied there.
-            static_assert(KC == 16, "two 16-byte loads of the order table per chunk");
+            constexpr int KQ = 4;                  // inputs per lane and chunk
+            const int kk0 = 8 * pg + KQ * b;       // first of them within the chunk
+            float2 pre[V2_D][KQ];
             const uint32_t mm0 = tc::smem_u32(MM);
-            auto orders = [&](int ch, int(&mo)[KC]) {
-#pragma unroll
-                for (int q2 = 0; q2 < 2; ++q2) {
-                    const uint4 q4 = lds_u4(mm0 + 2 * KC * ch + 16 * q2);
-                    const uint32_t wv[4] = {q4.x, q4.y, q4.z, q4.w};
-#pragma unroll
-                    for (int h = 0; h < 8; ++h) mo[8 * q2 + h] = (int)(short)(wv[h >> 1] >> (16 * (h & 1)));
-                }
+            // orders m' of this lane's inputs (one 8-byte load of the order table)
+            auto orders = [&](int ch, int(&mo)[KQ]) {
+                uint32_t w0, w1;
+                asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(w0), "=r"(w1) : "r"(mm0 + 2 * (V2_KC * ch + kk0)));
+                mo[0] = (int)(short)(w0 & 0xffff);
+                mo[1] = (int)(short)(w0 >> 16);
+                mo[2] = (int)(short)(w1 & 0xffff);
+                mo[3] = (int)(short)(w1 >> 16);
             };
-            auto fetch = [&](int ch, float2(&v)[KH]) {
-                if (krev) ch = nchunk - 1 - ch;
-                int mo[KC];
+            // input (n', m') reads the expansion at (n', +-m'): index k or k - 2m'.
+            // Loads are unconditional (from a clamped address) so that they stay in
+            // flight until their use V2_D chunks later; the mask is applied there.
+            auto fetch = [&](int c, float2(&v)[KQ]) {
+                const int ch = krev ? nchunk - 1 - c : c;
+                int mo[KQ];
                 orders(ch, mo);
 #pragma unroll
-                for (int h = 0; h < KH; ++h) {
-                    const int k = min(KC * ch + b * KH + h, P - 1);
-                    const int m = b ? mo[KH + h] : mo[h];
-                    const cf *a = valid ? src + (neg ? k - 2 * m : k) : pme;
+                for (int h = 0; h < KQ; ++h) {
+                    const int k = min(V2_KC * ch + kk0 + h, P - 1);
+                    const cf *a = valid ? src + (neg ? k - 2 * mo[h] : k) : pme;
                     v[h] = *(const float2 *)a;
                 }
             };
 #pragma unroll
             for (int u = 0; u < V2_D; ++u)
-                if (u < nmine) fetch(cfirst + u * V2_PG, pre[u]);
-            for (int q0 = 0; q0 < nmine && !failed; q0 += V2_D) {
+                if (u < nchunk) fetch(u, pre[u]);
+            for (int c0 = 0; c0 < nchunk && !failed; c0 += V2_D) {
 #pragma unroll
                 for (int u = 0; u < V2_D; ++u) {
-                    const int qq = q0 + u;
-                    if (qq >= nmine) break;
-                    const int ch = krev ? nchunk - 1 - (cfirst + qq * V2_PG) : cfirst + qq * V2_PG;   // data chunk
-                    bool okw = !xwrapped || tc::mbar_wait(&xempty[xs], xph ^ 1, WAIT_POLLS);
+                    const int c = c0 + u;
+                    if (c >= nchunk) break;
+                    const int ch = krev ? nchunk - 1 - c : c;   // data chunk
+                    bool okw = g < (uint32_t)V2_SX || tc::mbar_wait(&xempty[xs], xph ^ 1, WAIT_POLLS);
                     if (__any_sync(0xffffffffu, !okw)) {
                         failed = true;
                         break;
                     }
                     tc::fence_after();
-                    int mo[KC];
+                    int mo[KQ];
                     orders(ch, mo);
-                    // this lane's half of the products; the partner's half comes by shuffle
-                    cf mine[KH];
+                    // the lane's four inputs, phase-shifted and split once: word j of
+                    // input h holds piece j of (Re, Im)
+                    uint32_t own[KQ][V2_NPC], oth[KQ][V2_NPC];
 #pragma unroll
-                    for (int h = 0; h < KH; ++h) {
-                        const int kk = b * KH + h;
-                        cf v{0.f, 0.f};
-                        if (valid && KC * ch + kk < P) {
-                            const int m = b ? mo[KH + h] : mo[h];
-                            v = lds_cf(gr + 8 * (neg ? -m : m)) * cf{pre[u][h].x, pre[u][h].y};
-                        }
-                        mine[h] = v;
+                    for (int h = 0; h < KQ; ++h) {
+                        cf y{0.f, 0.f};
+                        if (valid && V2_KC * ch + kk0 + h < P)
+                            y = lds_cf(gr + 8 * (neg ? -mo[h] : mo[h])) * cf{pre[u][h].x, pre[u][h].y};
+                        v2_split_bf16(y.x, y.y, own[h]);
                     }
-                    // tensor-memory slot: per K-step of 16 real K (8 inputs) 8 columns of
-                    // bf16 pairs for each of the 3 pieces; input kk -> (row 2c: Re, -Im;
-                    // row 2c+1: Im, Re), even K in the low half
-                    // One K-step at a time (24 words live), stores aligned to their width.
+#pragma unroll
+                    for (int h = 0; h < KQ; ++h)
+#pragma unroll
+                        for (int pc = 0; pc < V2_NPC; ++pc) oth[h][pc] = __shfl_xor_sync(0xffffffffu, own[h][pc], 1);
+                    // the K-step's eight inputs in this lane's row: (Re, -Im) = negated
+                    // high half, (Im, Re) = swapped halves (the split of -x is -split x);
+                    // tensor-memory columns piece-major, even K in the low half
+                    uint32_t rw[8 * V2_NPC];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+#pragma unroll
+                        for (int pc = 0; pc < V2_NPC; ++pc) {
+                            const uint32_t wv = (i < KQ) == (b == 0) ? own[i & (KQ - 1)][pc] : oth[i & (KQ - 1)][pc];
+                            rw[i + 8 * pc] = b ? __byte_perm(wv, 0, 0x1032) : (wv ^ 0x80000000u);
+                        }
+                    const uint32_t ta = lane_base + XB + V2_XW * xs + 8 * V2_NPC * pg;
                     static_assert(V2_KS == 2 && V2_NPC == 3, "two K-steps of 24 columns per chunk");
-#pragma unroll
-                    for (int st = 0; st < V2_KS; ++st) {
-                        const bool own = (st == 0) == (b == 0);
-                        uint32_t rw[8 * V2_NPC];
-#pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            const cf o{__shfl_xor_sync(0xffffffffu, mine[i].x, 1),
-                                       __shfl_xor_sync(0xffffffffu, mine[i].y, 1)};
-                            const cf y = own ? mine[i] : o;
-                            uint32_t w[V2_NPC];
-                            v2_split_bf16(b ? y.y : y.x, b ? y.x : -y.y, w);
-#pragma unroll
-                            for (int pc = 0; pc < V2_NPC; ++pc) rw[i + 8 * pc] = w[pc];
-                        }
-                        const uint32_t ta = lane_base + XB + V2_XW * xs + 8 * V2_NPC * st;
-                        if (st == 0) {
-                            tc::tmem_st16(ta, rw);
-                            tc::tmem_st8(ta + 16, rw + 16);
-                        } else {
-                            tc::tmem_st8(ta, rw);
-                            tc::tmem_st16(ta + 8, rw + 8);
-                        }
+                    if (pg == 0) {
+                        tc::tmem_st16(ta, rw);
+                        tc::tmem_st8(ta + 16, rw + 16);
+                    } else {
+                        tc::tmem_st8(ta, rw);
+                        tc::tmem_st16(ta + 8, rw + 8);
                     }
                     tc::tmem_st_wait();
                     tc::fence_before();
                     tc::mbar_arrive(&xfull[xs]);
-                    // the group's next chunk is V2_PG ring slots further on
-                    xs += V2_PG;
-                    if (xs >= V2_SX) {
-                        xs -= V2_SX;
+                    ++g;
+                    if (++xs == V2_SX) {
+                        xs = 0;
                         xph ^= 1;
-                        xwrapped = true;
                     }
-                    if (qq + V2_D < nmine) fetch(cfirst + (qq + V2_D) * V2_PG, pre[u]);
+                    if (c + V2_D < nchunk) fetch(c + V2_D, pre[u]);
                 }
             }
         }

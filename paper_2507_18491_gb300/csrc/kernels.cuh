@@ -48,6 +48,7 @@ struct BoxDev {
     int layer, pad;
 };
 
+
 struct GemmWork {       // M2M / L2L: pairs [pair0, pair0 + npair) of one translation group
     int group, npair;
     int64_t pair0;
@@ -99,6 +100,16 @@ template <typename T>
 void launch_l2p(int p, int64_t nleaf, const int64_t *leaves, const BoxDev *boxes,
                 const double *xyz, const cx<T> *le, const MediumDev &M, const LayerScale &ls,
                 cd *phih, cudaStream_t st, bool p2m_basis = false, bool accumulate = false);
+
+// k_leaf.cu: L2P of the mixed form for p <= 15 (FP32 expansions), one thread per
+// sorted point (pt_box: its leaf box): ph (cd [N][3]) = the expansions le (cf
+// [box][3][P]) evaluated at the points (added with accumulate).  conj_basis /
+// scale select P2M's functions (conj Y, 4 pi: the transpose of P2M) or L2P's (Y, 1).
+bool leaf_fast_supported(int p);
+cudaError_t configure_leaf_fast();
+void launch_l2p_fast(int p, int64_t N, const int *pt_box, const BoxDev *boxes, const double *xyz, const cf *le,
+                     const MediumDev &M, const LayerScale &ls, cd *ph, bool conj_basis, double scale, bool accumulate,
+                     cudaStream_t st);
 
 // k_trans.cu
 cudaError_t configure_trans_kernels();
