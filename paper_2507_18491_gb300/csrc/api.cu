@@ -27,7 +27,9 @@ struct DevState {
     int64_t *leaves = nullptr;
     int64_t nleaves = 0;
     int *pt_box = nullptr;           // leaf box of every sorted point (mixed form)
-    bool leaf_fast = false;          // mixed form, p <= 15: L2P of k_leaf.cu
+    LeafUnit *units = nullptr;       // P2M units: at most 128 points of one leaf, largest first
+    int64_t nunits = 0;
+    bool leaf_fast = false;          // mixed form, p <= 15: P2M and L2P of k_leaf.cu
     cd *qh = nullptr, *ph = nullptr; // helical, sorted [N][3]
     void *me = nullptr, *le = nullptr; // [nbox][3][P], complex T (scaled)
     CompDev *comps = nullptr;
@@ -39,6 +41,7 @@ struct DevState {
     int64_t n_m2lwork = 0;
     void *tup = nullptr, *tdn = nullptr;   // [ngroup][P][P], complex T (scaled)
     void *tupT = nullptr, *tdnT = nullptr; // their transposes (SIMT forms: the transposed operator)
+    float *yscr = nullptr;           // persistent kernel: per-CTA accumulator scratch
     int64_t *tchild = nullptr, *tparent = nullptr;
     GemmWork *gwork = nullptr;
     std::vector<int64_t> gwork_off;  // per child level: [off[l], off[l+1])
@@ -62,7 +65,6 @@ struct DevState {
     int *flag = nullptr;
     int *mvstatus = nullptr;         // matvec status word (bit 4: tensor-core wait gave up)
     int m2l_kernel = 0;              // 0 FP64 SIMT, 1 FP32 SIMT, 2 tcgen05 streamed, 3 tcgen05 persistent
-    float *yscr = nullptr;           // persistent kernel: per-CTA accumulator scratch
     cf *ephase = nullptr;            // persistent kernel: e^{i d phi} per pair, d = -(p+2)..p+2
     int nsm = 0;
     cd *stage = nullptr;             // [2][N][3] for host-buffer matvec
@@ -488,11 +490,19 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
     d->nleaves = (int64_t)leaves.size();
     if (ctx->prm.precision == LMFMM_MIXED && leaf_fast_supported(p)) {
         std::vector<int> ptb(N > 0 ? N : 1, 0);
+        std::vector<LeafUnit> units;
         for (int64_t li : leaves) {
             const Box &b = ctx->boxes[li];
             for (int64_t q = b.p0; q < b.p1; ++q) ptb[q] = (int)li;
+            for (int64_t c0 = b.p0; c0 < b.p1; c0 += 128)
+                units.push_back(LeafUnit{c0, std::min<int64_t>(c0 + 128, b.p1), (int)li, b.p1 - b.p0 <= 128 ? 1 : 0});
         }
+        // largest units first, so that the last wave is made of small ones
+        std::stable_sort(units.begin(), units.end(),
+                         [](const LeafUnit &a, const LeafUnit &b) { return a.i1 - a.i0 > b.i1 - b.i0; });
         TRY(dupload(ctx, &d->pt_box, ptb));
+        TRY(dupload(ctx, &d->units, units));
+        d->nunits = (int64_t)units.size();
         d->leaf_fast = true;
     }
     TRY(dalloc(ctx, &d->qh, 3 * N));
@@ -814,14 +824,22 @@ lmfmm_status lmfmm_build(lmfmm_ctx *ctx, void *stream)
 }
 
 extern "C++" {
-// P2M / L2P at the leaves (per-leaf kernels; the mixed form's L2P runs one
-// thread per point, k_leaf.cu, where it applies).  l2p_basis / p2m_basis: the
-// transposes.
+// P2M / L2P at the leaves: the mixed form's kernels of k_leaf.cu where they
+// apply (P2M one warp per unit of a leaf, L2P one thread per point), else one
+// CTA per leaf.  l2p_basis / p2m_basis: the transposes.
 template <typename T>
 static void leaf_p2m(lmfmm_ctx *ctx, const cd *in, cx<T> *out, bool l2p_basis, cudaStream_t st)
 {
     DevState *d = DS(ctx);
-    launch_p2m<T>(ctx->prm.p, d->nleaves, d->leaves, d->boxes, d->xyz, in, ctx->med, d->lscale, out, st, l2p_basis);
+    const int p = ctx->prm.p;
+    if constexpr (std::is_same<T, float>::value) {
+        if (d->leaf_fast) {
+            launch_p2m_fast(p, d->nunits, d->units, d->boxes, d->xyz, in, ctx->med, d->lscale, out, !l2p_basis,
+                            l2p_basis ? 1.0 : 4.0 * 3.14159265358979323846, st);
+            return;
+        }
+    }
+    launch_p2m<T>(p, d->nleaves, d->leaves, d->boxes, d->xyz, in, ctx->med, d->lscale, out, st, l2p_basis);
 }
 
 template <typename T>

@@ -1,4 +1,4 @@
-// L2P of the mixed form (FP32 expansions), one code path per truncation p.
+// P2M and L2P of the mixed form (FP32 expansions), one code path per truncation p.
 //
 // Basis (Section 3.3, eqs. mecoeff and maxwell_LE_layered): for a point at r
 // relative to its leaf centre,
@@ -6,13 +6,16 @@
 // (times (-1)^m for m < 0), s = |k| S_leaf; P2M takes conj(Y) and scale 4 pi,
 // L2P takes Y and scale 1 (the transposes swap the two).
 //
-// k_l2p_pt is organised so that no barrier separates the phases of a point and
-// leaves of any size fill the machine (the leaves of a clustered point set hold
-// from one to several hundred points): one thread per point over the whole
-// sorted point set; the thread walks the orders m and, for each, the Legendre
-// recurrence in n, contracting the basis with its leaf's three local
-// expansions as it goes (the expansions are read through L1: the threads of a
-// warp mostly share a leaf).
+// Both kernels keep every SM busy whatever the leaf sizes (the leaves of a
+// clustered point set hold from one to several hundred points) and put no
+// barrier between the phases of a point:
+//   k_l2p_pt  one thread per point over the whole sorted point set; the thread
+//             walks the orders m and, for each, the Legendre recurrence in n,
+//             contracting the basis with its leaf's three local expansions as
+//             it goes (read through L1: the threads of a warp mostly share a leaf);
+//   k_p2m_ms  one warp per unit of at most 128 points of one leaf (units largest
+//             first); each lane keeps the coefficients of its own pair of orders
+//             in registers over a stream of points (see the kernel).
 // The recurrence coefficients live in constant memory and every loop over
 // (n, m) is unrolled for the compile-time p, so they are immediate operands.
 #include <cmath>
@@ -34,6 +37,10 @@ constexpr int LF_NT = (LF_PMAX + 1) * (LF_PMAX + 2) / 2;
 // series of j_n: ratio of consecutive terms -z^2/2 / (k (2n + 2k + 1)), leading 1/(2n+1)!!
 __constant__ float c_la[LF_NT], c_lb[LF_NT], c_ld[LF_PMAX + 1], c_lc[LF_PMAX + 1];
 __constant__ float c_sk[(LF_PMAX + 1) * LF_SER], c_idf[LF_PMAX + 1];
+// the same recurrence per (step t = n - m, order m), for lanes that each run
+// their own order: [t][m] = (a, b) with P_{m+t}^m = a (x P_{m+t-1}^m - b P_{m+t-2}^m)
+// (t = 1: a = d_m, b = 0), read through L1
+__device__ float2 g_lab[(LF_PMAX + 1) * (LF_PMAX + 1)];
 
 }  // namespace
 
@@ -57,7 +64,17 @@ cudaError_t configure_leaf_kernels()
         idf[m] = (float)(1.0 / df);
         for (int k = 1; k <= LF_SER; ++k) sk[m * LF_SER + k - 1] = (float)(1.0 / (k * (2.0 * m + 2.0 * k + 1.0)));
     }
+    float2 lab[(LF_PMAX + 1) * (LF_PMAX + 1)];
+    for (int t = 0; t <= LF_PMAX; ++t)
+        for (int m = 0; m <= LF_PMAX; ++m) {
+            const int n = m + t;
+            float2 v{0.f, 0.f};
+            if (t == 1 && n <= LF_PMAX) v = float2{ld[m], 0.f};
+            else if (t >= 2 && n <= LF_PMAX) v = float2{la[n * (n + 1) / 2 + m], lb[n * (n + 1) / 2 + m]};
+            lab[t * (LF_PMAX + 1) + m] = v;
+        }
     cudaError_t e;
+    if ((e = cudaMemcpyToSymbol(g_lab, lab, sizeof(lab))) != cudaSuccess) return e;
     if ((e = cudaMemcpyToSymbol(c_la, la, sizeof(la))) != cudaSuccess) return e;
     if ((e = cudaMemcpyToSymbol(c_lb, lb, sizeof(lb))) != cudaSuccess) return e;
     if ((e = cudaMemcpyToSymbol(c_ld, ld, sizeof(ld))) != cudaSuccess) return e;
@@ -182,6 +199,144 @@ __global__ void __launch_bounds__(128) k_l2p_pt(int64_t N, const int *pt_box, co
 
 namespace {
 
+// P2M (or the transpose of L2P): M[v][nm] = sum_j q_j[v] b_nm(r_j) over the
+// points of one unit (at most 128 points of one leaf), one warp per unit.
+// Lane = 16 s + 8 h + j: stream s takes the points s, s + 2, ...; h is the sign
+// of the order and {j, p - j} the lane's pair of orders, whose p + 2
+// coefficients (two runs of the Legendre recurrence in n) times the three
+// helical components stay in registers until the unit ends: no reduction over
+// points until then.  The warp first forms the seeds of 32 points at a time
+// (lane = point) in shared memory: cos theta, P^_m^m, e^{-i m phi} (or
+// e^{i m phi}), the radial factors and the charges.
+template <int PP>
+struct P2mSeeds {
+    static constexpr int W = 33;    // rows padded: lanes of one point reading different rows hit different banks
+    float x[W], pm[PP + 1][W];
+    cf jr[PP + 1][W], em[PP + 1][W], q[3][W];
+};
+
+template <int PP>
+__global__ void __launch_bounds__(32, 12) k_p2m_ms(const LeafUnit *units, const BoxDev *boxes, const double *xyz,
+                                                   const cd *qh, MediumDev M, LayerScale ls, cf *me, int conj_basis,
+                                                   double scale)
+{
+    constexpr int P = (PP + 1) * (PP + 1), NS = PP + 2;
+    __shared__ P2mSeeds<PP> sd;
+    const LeafUnit u = units[blockIdx.x];
+    const BoxDev b = boxes[u.box];
+    const cd k = M.k[b.layer];
+    const double inv_s = 1.0 / ls.s[b.layer];
+    const int lane = threadIdx.x, st = lane >> 4, hs = (lane >> 3) & 1, j = lane & 7;
+    const bool live = j <= PP / 2;
+    const int m1 = live ? j : 0, m2 = live ? PP - j : PP;   // idle lanes keep in-range orders
+    const bool run1 = live && !(hs == 1 && m1 == 0);       // +-m1 (no -0)
+    const bool run2 = live && m2 != m1;
+    const int seg1 = PP - m1 + 1;                           // steps of the first run
+    cf acc[NS][3];
+#pragma unroll
+    for (int t = 0; t < NS; ++t)
+#pragma unroll
+        for (int v = 0; v < 3; ++v) acc[t][v] = cf{0.f, 0.f};
+    for (int64_t c0 = u.i0; c0 < u.i1; c0 += 32) {
+        const int np = (int)min((int64_t)32, u.i1 - c0);
+        __syncwarp();
+        if (lane < np) {
+            const int64_t i = c0 + lane;
+            float x, sv;
+            cf e1, jr[PP + 1];
+            leaf_seed<PP>(k, xyz[3 * i] - b.c[0], xyz[3 * i + 1] - b.c[1], xyz[3 * i + 2] - b.c[2], conj_basis != 0,
+                          scale, inv_s, x, sv, e1, jr);
+            sd.x[lane] = x;
+            float pmm = c_lc[0];
+            cf em{1.f, 0.f};
+#pragma unroll
+            for (int m = 0; m <= PP; ++m) {
+                if (m > 0) {
+                    pmm = -pmm * sv * c_lc[m];
+                    em = em * e1;
+                }
+                sd.pm[m][lane] = pmm;
+                sd.em[m][lane] = em;
+                sd.jr[m][lane] = jr[m];
+            }
+#pragma unroll
+            for (int v = 0; v < 3; ++v) sd.q[v][lane] = cf{(float)qh[3 * i + v].x, (float)qh[3 * i + v].y};
+        }
+        __syncwarp();
+        for (int pj = st; pj < np; pj += 2) {
+            const float x = sd.x[pj];
+            const cf q0 = sd.q[0][pj], q1 = sd.q[1][pj], q2 = sd.q[2][pj];
+            // azimuthal factor of a run: e^{i m phi}, or (-1)^m conj of it for -m
+            auto fac = [&](int m) {
+                const cf e = sd.em[m][pj];
+                return hs == 0 ? e : ((m & 1) ? cf{-e.x, e.y} : cf{e.x, -e.y});
+            };
+            cf f = fac(m1);
+            float p0 = 0.f, p1 = 0.f;
+#pragma unroll
+            for (int t = 0; t < NS; ++t) {
+                const bool first = t < seg1;
+                const int m = first ? m1 : m2;
+                const int tn = first ? t : t - seg1;   // step within the run, n = m + tn
+                if (t == seg1) {
+                    f = fac(m2);
+                    p0 = p1 = 0.f;
+                }
+                float pl;
+                if (tn == 0) {
+                    pl = sd.pm[m][pj];
+                } else {
+                    const float2 ab = __ldg(&g_lab[tn * (LF_PMAX + 1) + m]);
+                    pl = ab.x * (x * p1 - ab.y * p0);
+                }
+                p0 = p1;
+                p1 = pl;
+                if (first ? run1 : run2) {
+                    const cf bv = (pl * sd.jr[m + tn][pj]) * f;
+                    acc[t][0] += q0 * bv;
+                    acc[t][1] += q1 * bv;
+                    acc[t][2] += q2 * bv;
+                }
+            }
+        }
+    }
+    // the two streams hold the same coefficients: add them, then stream 0 writes
+#pragma unroll
+    for (int t = 0; t < NS; ++t)
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+            acc[t][v].x += __shfl_xor_sync(0xffffffffu, acc[t][v].x, 16);
+            acc[t][v].y += __shfl_xor_sync(0xffffffffu, acc[t][v].y, 16);
+        }
+    if (st != 0) return;
+    cf *out = me + (int64_t)u.box * 3 * P;
+#pragma unroll
+    for (int t = 0; t < NS; ++t) {
+        const bool first = t < seg1;
+        const int m = first ? m1 : m2;
+        const int n = m + (first ? t : t - seg1);
+        if (!(first ? run1 : run2)) continue;
+        const int idx = n * n + n + (hs ? -m : m);
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+            if (u.whole) {
+                out[v * P + idx] = acc[t][v];
+            } else {
+                atomicAdd(&out[v * P + idx].x, acc[t][v].x);
+                atomicAdd(&out[v * P + idx].y, acc[t][v].y);
+            }
+        }
+    }
+}
+
+template <int PP>
+void launch_p2m_pp(int64_t nunit, const LeafUnit *units, const BoxDev *boxes, const double *xyz, const cd *qh,
+                   const MediumDev &M, const LayerScale &ls, cf *me, bool conj_basis, double scale, cudaStream_t st)
+{
+    if (nunit <= 0) return;
+    k_p2m_ms<PP><<<(unsigned)nunit, 32, 0, st>>>(units, boxes, xyz, qh, M, ls, me, conj_basis ? 1 : 0, scale);
+}
+
 template <int PP>
 void launch_l2p_pp(int64_t N, const int *pt_box, const BoxDev *boxes, const double *xyz, const cf *le,
                    const MediumDev &M, const LayerScale &ls, cd *ph, bool conj_basis, double scale, bool accumulate,
@@ -204,6 +359,21 @@ void launch_l2p_fast(int p, int64_t N, const int *pt_box, const BoxDev *boxes, c
 #define LF_CASE(v)                                                                                           \
     case v:                                                                                                  \
         launch_l2p_pp<v>(N, pt_box, boxes, xyz, le, M, ls, ph, conj_basis, scale, accumulate, st);           \
+        break;
+        LF_CASES(LF_CASE)
+#undef LF_CASE
+    default: break;
+    }
+}
+
+void launch_p2m_fast(int p, int64_t nunit, const LeafUnit *units, const BoxDev *boxes, const double *xyz,
+                     const cd *qh, const MediumDev &M, const LayerScale &ls, cf *me, bool conj_basis, double scale,
+                     cudaStream_t st)
+{
+    switch (p) {
+#define LF_CASE(v)                                                                                           \
+    case v:                                                                                                  \
+        launch_p2m_pp<v>(nunit, units, boxes, xyz, qh, M, ls, me, conj_basis, scale, st);                    \
         break;
         LF_CASES(LF_CASE)
 #undef LF_CASE

@@ -48,6 +48,11 @@ struct BoxDev {
     int layer, pad;
 };
 
+struct LeafUnit {       // P2M work of one warp: points [i0, i1) (at most 128) of leaf box
+    int64_t i0, i1;
+    int box, whole;     // whole: the unit covers the leaf (plain stores, else atomics)
+};
+
 
 struct GemmWork {       // M2M / L2L: pairs [pair0, pair0 + npair) of one translation group
     int group, npair;
@@ -101,7 +106,7 @@ void launch_l2p(int p, int64_t nleaf, const int64_t *leaves, const BoxDev *boxes
                 const double *xyz, const cx<T> *le, const MediumDev &M, const LayerScale &ls,
                 cd *phih, cudaStream_t st, bool p2m_basis = false, bool accumulate = false);
 
-// k_leaf.cu: L2P of the mixed form for p <= 15 (FP32 expansions), one thread per
+// k_leaf.cu: P2M and L2P of the mixed form for p <= 15 (FP32 expansions), one thread per
 // sorted point (pt_box: its leaf box): ph (cd [N][3]) = the expansions le (cf
 // [box][3][P]) evaluated at the points (added with accumulate).  conj_basis /
 // scale select P2M's functions (conj Y, 4 pi: the transpose of P2M) or L2P's (Y, 1).
@@ -109,6 +114,11 @@ bool leaf_fast_supported(int p);
 cudaError_t configure_leaf_fast();
 void launch_l2p_fast(int p, int64_t N, const int *pt_box, const BoxDev *boxes, const double *xyz, const cf *le,
                      const MediumDev &M, const LayerScale &ls, cd *ph, bool conj_basis, double scale, bool accumulate,
+                     cudaStream_t st);
+// P2M of the mixed form for p <= 15: one warp per unit, me (cf [box][3][P], zeroed
+// beforehand) += the coefficients of the helical charges qh (cd, sorted)
+void launch_p2m_fast(int p, int64_t nunit, const LeafUnit *units, const BoxDev *boxes, const double *xyz,
+                     const cd *qh, const MediumDev &M, const LayerScale &ls, cf *me, bool conj_basis, double scale,
                      cudaStream_t st);
 
 // k_trans.cu
