@@ -332,11 +332,13 @@ def main():
     m2l_s = float(np.mean(m2l_ms)) * 1e-3
     achieved = flops / m2l_s / 1e12
     kern = {0: "k_m2l<double>", 1: "k_m2l<float>", 2: "k_m2l_tc", 3: "k_m2l_tc2"}[st["m2l_kernel"]]
-    # DRAM bytes per launch of k_m2l_tc2: the table image times the read+write / image
-    # ratio of an ncu capture of the same kernel (dram__bytes_read.sum 3.864 GB +
-    # dram__bytes_write.sum 0.067 GB for a 3.691 GB image, three-layer N = 8192,
-    # p = 12, depth 4); other kernels: not captured
-    traffic = st["bytes_tables"] * (3.931 / 3.691) if st["m2l_kernel"] == 3 else None
+    # DRAM bytes per launch of k_m2l_tc2: the table image times the read + write / image
+    # ratio of an ncu capture of the same kernel (dram__bytes_read.sum 2.780 GB +
+    # dram__bytes_write.sum 0.042 GB for a 2.622 GB image, three-layer N = 8192,
+    # p = 12, depth 4, theta 0.55).  The image, read once per launch, is most of it; the
+    # multipole expansions fit in L2 in that case but not at N = 2^20 (152 MB), so the
+    # scaled figure is a lower bound there.  Other kernels: not captured
+    traffic = st["bytes_tables"] * (2.8226 / 2.6224) if st["m2l_kernel"] == 3 else None
     bound = "tensor" if st["m2l_kernel"] >= 2 else "alu"
     if prec == lmfmm.FP64:
         peak, peak_src = FP64_PEAK_TFLOPS, "derived (not measured) FP64 ALU: 152 SM x 2 FMA/clk x 2 x 2070 MHz"
