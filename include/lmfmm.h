@@ -46,8 +46,10 @@ typedef enum {
     LMFMM_ERR_STATE = -4,        /* calls made in the wrong order */
     LMFMM_ERR_QUAD = -5,         /* a bounded quadrature hit its node cap (quad_node_cap) */
     LMFMM_ERR_UNSUPPORTED = -6,  /* request outside what this build implements */
-    LMFMM_ERR_TIMEOUT = -7       /* a bounded device wait of the tensor-core pipeline gave up:
+    LMFMM_ERR_TIMEOUT = -7,      /* a bounded device wait of the tensor-core pipeline gave up:
                                     the result of the checked calls is invalid */
+    LMFMM_ERR_INTERNAL = -8      /* a consistency check of the library's own setup structures
+                                    failed (lmfmm_plan_check) */
 } lmfmm_status;
 
 typedef struct lmfmm_ctx lmfmm_ctx;
@@ -295,6 +297,59 @@ lmfmm_status lmfmm_free_m2l_table(int p, lmfmm_c128 k, double rho, double dz, lm
                                    lmfmm_c128 *blocks);
 
 lmfmm_status lmfmm_get_stats(const lmfmm_ctx *ctx, lmfmm_stats *out);
+
+/* ------------------------------------------------------------- plan check
+ * The setup structures of lmfmm_build, built and checked on the host alone (no
+ * device is touched, no context is kept): the per-layer octrees over the sorted
+ * points, the dual traversal of every reaction component (l, l', *, star) into
+ * far box pairs and near leaf pairs (Sections 3.3 and 3.4.1; admissibility as in
+ * lmfmm_params), the distinct M2L geometries and their pair lists, the
+ * free-space lists when params->components asks for them (Section 2), the
+ * M2M / L2L translation groups and the 64-column M2L work items of the
+ * persistent tensor-core kernel.  Checks:
+ *   tree       every layer's points are partitioned by the boxes of each level,
+ *              children partition their parent, every point lies in its leaf's
+ *              cell, box radii bound their points;
+ *   coverage   every (component, source leaf, target leaf) triple is reached by
+ *              exactly one far pair of some ancestor pair or one near pair (the
+ *              FMM's split of the double sum), likewise every same-layer leaf
+ *              pair of the free-space part;
+ *   geometry   every far pair meets the admissibility test and has the
+ *              horizontal distance, mapped heights (or, within a layer, height
+ *              offset) and direction of its geometry's table;
+ *   indices    every box, pair, geometry, coefficient offset and work-item range
+ *              a kernel reads is in bounds, and pair ranges tile their arrays.
+ * Arguments as lmfmm_create / lmfmm_set_layers / lmfmm_set_points (host xyz,
+ * [N][3] double); flags: 0, or the test hooks below, which remove one pair
+ * after the build so that a caller can see the check report it.  Coverage is
+ * checked per component and target leaf, as a tiling of the source leaves by
+ * the intervals its ancestors' far pairs and its near pairs reach, while a
+ * component has at most 2^25 such intervals (larger ones are counted in
+ * n_components_unchecked).  Host memory ~24 bytes per interval.  Returns
+ * LMFMM_OK when every check holds, LMFMM_ERR_INTERNAL when one fails (the
+ * count and the first failure are in *out), or the argument error of the
+ * corresponding context call (message in out->message). */
+enum { LMFMM_PLAN_DROP_FAR_PAIR = 1, LMFMM_PLAN_DROP_NEAR_PAIR = 2 };
+
+typedef struct {
+    int depth;                      /* leaf level */
+    int n_components;               /* reaction components */
+    int n_free_components;          /* free-space pseudo-components (one per layer with points) */
+    int n_components_unchecked;     /* components whose coverage was too large to check */
+    int64_t n_boxes;
+    int64_t n_leaves[9];            /* per layer (at most 9 layers) */
+    int64_t n_far_pairs, n_geometries, n_near_pairs, n_near_point_pairs;
+    int64_t n_free_far_pairs, n_free_geometries, n_free_near_pairs, n_free_near_point_pairs;
+    int64_t n_translation_pairs;    /* (child, parent) pairs of the M2M / L2L groups */
+    int64_t n_work_items, n_columns;   /* M2L work items (<= 64 helical columns) and columns */
+    int64_t n_leaf_pairs_checked;   /* (component, source leaf, target leaf) triples covered */
+    int64_t n_violations;           /* failed checks (0: consistent) */
+    double root_center[3], root_half;  /* root cell; leaves have side 2 root_half / 2^depth */
+    char message[256];              /* first failure or argument error, else empty */
+} lmfmm_plan_info;
+
+lmfmm_status lmfmm_plan_check(const lmfmm_params *prm, int L, const double *d, const lmfmm_c128 *k,
+                              int64_t N, const double *xyz, int flags, lmfmm_plan_info *out);
 
 /* ------------------------------------------------------------- batches
  * Many layered problems (own media, points, sizes; one device, one p, one

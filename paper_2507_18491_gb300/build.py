@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "liblmfmm.so")
-SOURCES = ["api.cu", "k_tab.cu", "k_fmm.cu", "k_leaf.cu", "k_trans.cu", "k_m2l_tc.cu", "k_grad.cu", "noalloc.cu",
+SOURCES = ["api.cu", "k_tab.cu", "k_fmm.cu", "k_leaf.cu", "k_trans.cu", "k_m2l_tc.cu", "k_grad.cu", "noalloc.cu", "plan.cpp",
            "host_setup.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -287,6 +287,12 @@ lmfmm_status tabulate(lmfmm_ctx *ctx, std::vector<GeomDev> &hg, const CompDev *d
 }  // namespace
 
 namespace lmf {
+// the M2L work items the matvec builds, for the host-side plan check (plan.cpp)
+int64_t plan_work_items(const lmfmm_ctx *ctx, int bn, std::vector<M2LWork> &mw)
+{
+    return m2l_work_items(ctx, bn, 0, mw);
+}
+
 // read-only view of the device state for lmfmm_direct_noalloc (noalloc.cu)
 bool noalloc_state(lmfmm_ctx *ctx, const int64_t **perm, const BoxDev **boxes, const double **xyz,
                    const CompDev **comps, cd **qh, cd **ph, int **flag)

@@ -141,6 +141,9 @@ void launch_m2l_tr(int p, int64_t nwork, const M2LWork *work, const GeomDev *geo
 // status gets bit 4 if a tensor-core wait gave up
 bool m2l_tc_supported(int p);
 int m2l_tc_cols();
+// M2L work items of a context whose host structures are built, cut to at most bn
+// helical columns, in the order the matvec launches them (api.cu)
+int64_t plan_work_items(const lmfmm_ctx *ctx, int bn, std::vector<M2LWork> &mw);
 cudaError_t configure_m2l_tc();
 cudaError_t launch_m2l_tc(int p, int64_t nwork, const M2LWork *work, const GeomDev *geoms,
                           const CompDev *comps, const M2LPair *pairs, const cf *tab, const cf *me,

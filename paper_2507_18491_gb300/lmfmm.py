@@ -16,8 +16,9 @@ from . import build as _build
 
 _lib = None
 
-OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_STATE, ERR_QUAD, ERR_UNSUPPORTED, ERR_TIMEOUT = (
-    0, -1, -2, -3, -4, -5, -6, -7)
+OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_STATE, ERR_QUAD, ERR_UNSUPPORTED, ERR_TIMEOUT, ERR_INTERNAL = (
+    0, -1, -2, -3, -4, -5, -6, -7, -8)
+PLAN_DROP_FAR_PAIR, PLAN_DROP_NEAR_PAIR = 1, 2
 FP64, MIXED = 0, 1
 C128, C64 = 0, 1
 REACTION, FREE, TOTAL = 0, 1, 2
@@ -49,12 +50,26 @@ class Stats(ctypes.Structure):
                 ("n_free_geometries", ctypes.c_int64), ("n_free_near_point_pairs", ctypes.c_int64)]
 
 
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("depth", ctypes.c_int), ("n_components", ctypes.c_int),
+                ("n_free_components", ctypes.c_int), ("n_components_unchecked", ctypes.c_int),
+                ("n_boxes", ctypes.c_int64), ("n_leaves", ctypes.c_int64 * 9),
+                ("n_far_pairs", ctypes.c_int64), ("n_geometries", ctypes.c_int64),
+                ("n_near_pairs", ctypes.c_int64), ("n_near_point_pairs", ctypes.c_int64),
+                ("n_free_far_pairs", ctypes.c_int64), ("n_free_geometries", ctypes.c_int64),
+                ("n_free_near_pairs", ctypes.c_int64), ("n_free_near_point_pairs", ctypes.c_int64),
+                ("n_translation_pairs", ctypes.c_int64), ("n_work_items", ctypes.c_int64),
+                ("n_columns", ctypes.c_int64), ("n_leaf_pairs_checked", ctypes.c_int64),
+                ("n_violations", ctypes.c_int64), ("root_center", ctypes.c_double * 3),
+                ("root_half", ctypes.c_double), ("message", ctypes.c_char * 256)]
+
+
 EXPORTS = ["lmfmm_default_params", "lmfmm_create", "lmfmm_set_layers", "lmfmm_set_points",
            "lmfmm_set_points_device", "lmfmm_build", "lmfmm_matvec", "lmfmm_matvec_host",
            "lmfmm_matvec_adjoint", "lmfmm_matvec_transpose", "lmfmm_gradient", "lmfmm_check", "lmfmm_test_set_status", "lmfmm_direct",
            "lmfmm_direct_noalloc", "lmfmm_densities", "lmfmm_m2l_table", "lmfmm_translation_matrix",
            "lmfmm_free_m2l_table",
-           "lmfmm_get_stats", "lmfmm_last_error", "lmfmm_destroy", "lmfmm_batch_create",
+           "lmfmm_get_stats", "lmfmm_plan_check", "lmfmm_last_error", "lmfmm_destroy", "lmfmm_batch_create",
            "lmfmm_batch_matvec", "lmfmm_batch_tune", "lmfmm_batch_check", "lmfmm_batch_info",
            "lmfmm_batch_last_error", "lmfmm_batch_destroy"]
 
@@ -101,6 +116,8 @@ def load():
         "lmfmm_translation_matrix": [i, _Complex128, ctypes.POINTER(d), P, P],
         "lmfmm_free_m2l_table": [i, _Complex128, d, d, P, P],
         "lmfmm_get_stats": [P, ctypes.POINTER(Stats)],
+        "lmfmm_plan_check": [ctypes.POINTER(Params), i, ctypes.POINTER(d), ctypes.POINTER(_Complex128), i64,
+                             ctypes.POINTER(d), i, ctypes.POINTER(PlanInfo)],
         "lmfmm_last_error": [P],
         "lmfmm_destroy": [P],
         "lmfmm_batch_create": [ctypes.POINTER(P), ctypes.POINTER(P), i],
@@ -305,6 +322,28 @@ def get_stats(ctx) -> dict:
     names = ["p2m", "m2m", "m2l", "l2l", "l2p", "s2t", "permute", "total"]
     out["ms_stage"] = {n: s.ms_stage[i] for i, n in enumerate(names)}
     return out
+
+
+def plan_check(d, k, xyz, p=8, depth=-1, leaf_cap=64, theta=0.55, eta=0.1, components=REACTION, flags=0):
+    """Host-only build and consistency check of the setup structures
+    (lmfmm_plan_check); returns (status, info dict).  Needs no GPU."""
+    prm = default_params()
+    prm.p, prm.depth, prm.leaf_cap = int(p), int(depth), int(leaf_cap)
+    prm.theta, prm.eta, prm.components = float(theta), float(eta), int(components)
+    d = np.ascontiguousarray(np.asarray(d, np.float64).reshape(-1))
+    k = np.asarray(k, np.complex128).reshape(-1)
+    karr = (_Complex128 * k.size)(*[_Complex128(float(v.real), float(v.imag)) for v in k])
+    xyz = np.ascontiguousarray(np.asarray(xyz, np.float64).reshape(-1, 3))
+    info = PlanInfo()
+    rc = load().lmfmm_plan_check(ctypes.byref(prm), int(d.size), d.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                 karr, int(xyz.shape[0]), xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                 int(flags), ctypes.byref(info))
+    out = {f: getattr(info, f) for f, _ in PlanInfo._fields_
+           if f not in ("n_leaves", "root_center", "message")}
+    out["n_leaves"] = list(info.n_leaves)[:d.size + 1]
+    out["root_center"] = list(info.root_center)
+    out["message"] = info.message.decode()
+    return rc, out
 
 
 def last_error(ctx=None) -> str:
