@@ -58,7 +58,8 @@ def tensor_peak(tf32):
 def workload(name, seed_shift=0):
     from paper_2507_18491_gb300 import workloads as W
     if name == "four_layer":
-        return W.four_layer_clusters(seed=1005 + seed_shift), dict(depth=6, theta=0.5)
+        # leaf level from the depth tuner (host-side cost model over depths 5-7)
+        return W.four_layer_clusters(seed=1005 + seed_shift), dict(depth="auto", depths=(5, 6, 7), theta=0.5)
     if name == "three_layer":
         return W.three_layer(seed=1002 + seed_shift), dict(depth=5, theta=0.45)
     if name == "four_layer_small":
@@ -274,6 +275,14 @@ def main():
         opt["theta"] = args.theta
     p = args.p or w.p
     prec = lmfmm.FP64 if args.precision == "fp64" else lmfmm.MIXED
+    tuner = None
+    if opt["depth"] == "auto":
+        # predicted matvec times of the mixed tensor-core form from the host-built
+        # structures' counts (lmfmm_plan_depth), before anything runs on the device
+        best, pred = lmfmm.plan_depth(w.d, w.k, w.xyz, p=p, depths=opt["depths"], theta=opt["theta"])
+        opt["depth"] = best
+        tuner = {"choice": best, "predicted_ms": {str(k): round(v, 3) for k, v in pred.items()},
+                 "model": "lmfmm_plan_depth default unit costs (measured on GB300, mixed form, p = 12)"}
     t0 = time.time()
     tck = {"tensor_cores": args.tensor_cores} if prec == lmfmm.MIXED else {}
     op = lmfmm.Operator(w.d, w.k, w.xyz, p=p, depth=opt["depth"], theta=opt["theta"],
@@ -353,7 +362,8 @@ def main():
         "vs_baseline": (value / PAPER_MTARGETS[w.name]) if w.name in PAPER_MTARGETS else None,
         "dtype": "f64" if prec == lmfmm.FP64 else "f32", "data": "synthetic",
         "config": {"workload": w.name, "N": w.N, "layers": int(w.d.size + 1), "p": p,
-                   "depth": st["depth"], "theta": opt["theta"], "precision": args.precision,
+                   "depth": st["depth"], "depth_tuner": tuner, "theta": opt["theta"],
+                   "precision": args.precision,
                    "tensor_cores": int(args.tensor_cores) if prec == lmfmm.MIXED else 0,
                    "components": st["n_components"], "m2l_pairs": st["n_m2l_pairs"],
                    "geometries": st["n_geometries"],

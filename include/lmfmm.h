@@ -351,6 +351,20 @@ typedef struct {
 lmfmm_status lmfmm_plan_check(const lmfmm_params *prm, int L, const double *d, const lmfmm_c128 *k,
                               int64_t N, const double *xyz, int flags, lmfmm_plan_info *out);
 
+/* Leaf-level tuner (host only): for every depth dmin..dmax (<= 10) the setup
+ * structures are built as above and the matvec time predicted from their counts,
+ *   t = u0 (M2L work items) + u1 (near point pairs, both parts) + u2 (M2M / L2L
+ *       child-parent pairs) + u3 N   [ns],
+ * with unit_ns = {u0, u1, u2, u3}, or NULL for costs measured on GB300 with the
+ * mixed form and the tensor-core M2L / M2M / L2L at p = 12 (about 80, 0.27, 14.7
+ * and 1.1 ns), scaled to other p by (P / 169)^2 (u0, u2) and P / 169 (u3).  The
+ * accuracy is set by theta and p, not by the depth.  predicted_ms[dmax - dmin + 1]
+ * receives the predictions, *best the depth of the smallest.  Errors as
+ * lmfmm_plan_check (LMFMM_ERR_ARG also for a bad depth range or NULL outputs). */
+lmfmm_status lmfmm_plan_depth(const lmfmm_params *prm, int L, const double *d, const lmfmm_c128 *k,
+                              int64_t N, const double *xyz, int dmin, int dmax, const double *unit_ns,
+                              int *best, double *predicted_ms);
+
 /* ------------------------------------------------------------- batches
  * Many layered problems (own media, points, sizes; one device, one p, one
  * precision) applied together.  lmfmm_batch_matvec records every problem's

@@ -498,3 +498,48 @@ extern "C" lmfmm_status lmfmm_plan_check(const lmfmm_params *prm, int L, const d
     delete ctx;
     return ck.n ? LMFMM_ERR_INTERNAL : LMFMM_OK;
 }
+
+// Depth tuner: predicted matvec time per candidate leaf level from the host
+// structures' counts and per-unit device costs.  Default costs (ns) are the
+// GB300 measurements of the mixed form with the tensor-core M2L, M2M and L2L at
+// p = 12 (four-layer N = 2^20 workload, depth 6: 8.79 ms of M2L over 109831 work
+// items; 0.754 ms of near field over 2782511 point pairs; 0.551 ms of M2M + L2L
+// over 37447 (child, parent) pairs; 1.154 ms of P2M, L2P and permutation over
+// 2^20 points), scaled to other p by (P / 169)^2 for the M2L and translations
+// and by P / 169 for the point terms.
+extern "C" lmfmm_status lmfmm_plan_depth(const lmfmm_params *prm, int L, const double *d, const lmfmm_c128 *k,
+                                         int64_t N, const double *xyz, int dmin, int dmax, const double *unit_ns,
+                                         int *best, double *predicted_ms)
+{
+    if (!prm || !best || !predicted_ms || dmin < 0 || dmax < dmin || dmax > 10) return LMFMM_ERR_ARG;
+    const double P = (double)((prm->p + 1) * (prm->p + 1)), r = P / 169.0;
+    const double dflt[4] = {8.79e6 / 109831 * r * r, 0.754e6 / 2782511, 0.551e6 / 37447 * r * r,
+                            1.154e6 / 1048576 * r};
+    const double *u = unit_ns ? unit_ns : dflt;
+    *best = -1;
+    double best_ms = 0;
+    for (int D = dmin; D <= dmax; ++D) {
+        lmfmm_params q = *prm;
+        q.depth = D;
+        lmfmm_ctx *ctx = new lmfmm_ctx();
+        ctx->prm = q;
+        lmfmm_status rc = lmfmm_set_layers(ctx, L, d, k);
+        if (rc == LMFMM_OK) rc = lmfmm_set_points(ctx, N, xyz);
+        if (rc == LMFMM_OK) rc = build_host_structures(ctx);
+        if (rc != LMFMM_OK) {
+            delete ctx;
+            return rc;
+        }
+        std::vector<M2LWork> mw;
+        plan_work_items(ctx, 64, mw);
+        const double ns = u[0] * (double)mw.size() + u[1] * (double)(ctx->n_near_pp + ctx->n_free_pp) +
+                          u[2] * (double)ctx->tpair_child.size() + u[3] * (double)N;
+        predicted_ms[D - dmin] = ns * 1e-6;
+        if (*best < 0 || ns * 1e-6 < best_ms) {
+            *best = D;
+            best_ms = ns * 1e-6;
+        }
+        delete ctx;
+    }
+    return LMFMM_OK;
+}

@@ -69,7 +69,7 @@ EXPORTS = ["lmfmm_default_params", "lmfmm_create", "lmfmm_set_layers", "lmfmm_se
            "lmfmm_matvec_adjoint", "lmfmm_matvec_transpose", "lmfmm_gradient", "lmfmm_check", "lmfmm_test_set_status", "lmfmm_direct",
            "lmfmm_direct_noalloc", "lmfmm_densities", "lmfmm_m2l_table", "lmfmm_translation_matrix",
            "lmfmm_free_m2l_table",
-           "lmfmm_get_stats", "lmfmm_plan_check", "lmfmm_last_error", "lmfmm_destroy", "lmfmm_batch_create",
+           "lmfmm_get_stats", "lmfmm_plan_check", "lmfmm_plan_depth", "lmfmm_last_error", "lmfmm_destroy", "lmfmm_batch_create",
            "lmfmm_batch_matvec", "lmfmm_batch_tune", "lmfmm_batch_check", "lmfmm_batch_info",
            "lmfmm_batch_last_error", "lmfmm_batch_destroy"]
 
@@ -118,6 +118,8 @@ def load():
         "lmfmm_get_stats": [P, ctypes.POINTER(Stats)],
         "lmfmm_plan_check": [ctypes.POINTER(Params), i, ctypes.POINTER(d), ctypes.POINTER(_Complex128), i64,
                              ctypes.POINTER(d), i, ctypes.POINTER(PlanInfo)],
+        "lmfmm_plan_depth": [ctypes.POINTER(Params), i, ctypes.POINTER(d), ctypes.POINTER(_Complex128), i64,
+                             ctypes.POINTER(d), i, i, ctypes.POINTER(d), ctypes.POINTER(i), ctypes.POINTER(d)],
         "lmfmm_last_error": [P],
         "lmfmm_destroy": [P],
         "lmfmm_batch_create": [ctypes.POINTER(P), ctypes.POINTER(P), i],
@@ -344,6 +346,27 @@ def plan_check(d, k, xyz, p=8, depth=-1, leaf_cap=64, theta=0.55, eta=0.1, compo
     out["root_center"] = list(info.root_center)
     out["message"] = info.message.decode()
     return rc, out
+
+
+def plan_depth(d, k, xyz, p=8, depths=(4, 5, 6, 7), theta=0.55, eta=0.1, components=REACTION, unit_ns=None):
+    """Leaf-level tuner (lmfmm_plan_depth, host only): returns (best depth,
+    {depth: predicted matvec ms})."""
+    prm = default_params()
+    prm.p, prm.theta, prm.eta, prm.components = int(p), float(theta), float(eta), int(components)
+    d = np.ascontiguousarray(np.asarray(d, np.float64).reshape(-1))
+    k = np.asarray(k, np.complex128).reshape(-1)
+    karr = (_Complex128 * k.size)(*[_Complex128(float(v.real), float(v.imag)) for v in k])
+    xyz = np.ascontiguousarray(np.asarray(xyz, np.float64).reshape(-1, 3))
+    d0, d1 = int(min(depths)), int(max(depths))
+    pred = (ctypes.c_double * (d1 - d0 + 1))()
+    best = ctypes.c_int()
+    u = None
+    if unit_ns is not None:
+        u = (ctypes.c_double * 4)(*[float(x) for x in unit_ns])
+    _check(load().lmfmm_plan_depth(ctypes.byref(prm), int(d.size), d.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                   karr, int(xyz.shape[0]), xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                   d0, d1, u, ctypes.byref(best), pred))
+    return best.value, {d0 + j: pred[j] for j in range(d1 - d0 + 1)}
 
 
 def last_error(ctx=None) -> str:

@@ -112,3 +112,27 @@ def test_bad_arguments_are_rejected():
     assert rc == lmfmm.ERR_ARG and "parameter" in info["message"]
     rc, info = lmfmm.plan_check(w.d, w.k, w.xyz, p=6, depth=2, flags=8)
     assert rc == lmfmm.ERR_ARG
+
+
+def test_depth_tuner_follows_its_cost_terms():
+    """With only the near-field term the deepest tree wins (fewest point pairs
+    per leaf pair), with only the M2L term the shallowest (fewest far pairs);
+    the predictions are the cost model applied to the plan's counts."""
+    w = W.three_layer(n=8192, seed=1002, p=6)
+    near_only, pn = lmfmm.plan_depth(w.d, w.k, w.xyz, p=6, depths=(2, 3, 4), theta=0.45, unit_ns=(0, 1, 0, 0))
+    m2l_only, pm = lmfmm.plan_depth(w.d, w.k, w.xyz, p=6, depths=(2, 3, 4), theta=0.45, unit_ns=(1, 0, 0, 0))
+    assert near_only == 4 and m2l_only == 2
+    for D in (2, 3, 4):
+        rc, info = lmfmm.plan_check(w.d, w.k, w.xyz, p=6, depth=D, theta=0.45)
+        assert rc == lmfmm.OK
+        assert pn[D] == pytest.approx(info["n_near_point_pairs"] * 1e-6, rel=1e-12)
+        assert pm[D] == pytest.approx(info["n_work_items"] * 1e-6, rel=1e-12)
+
+
+def test_depth_tuner_picks_the_benchmark_depth():
+    """With the costs measured on GB300, the four-layer benchmark's tuned leaf
+    level is depth 6 (the level its full-size parity test runs)."""
+    w = W.four_layer_clusters(seed=1005)
+    best, pred = lmfmm.plan_depth(w.d, w.k, w.xyz, p=12, depths=(5, 6, 7), theta=0.5)
+    assert best == 6 and min(pred, key=pred.get) == 6
+    assert 9.0 < pred[6] < 14.0    # measured: 11.3 ms per matvec at depth 6
