@@ -38,6 +38,13 @@ using ll = long long;
 
 bool close_to(double a, double b, double scale) { return std::fabs(a - b) <= 1e-11 * scale; }
 
+// coordinate magnitude of the point set: rounding of centres and their
+// differences is relative to it, whatever the cell size
+double coord_scale(const lmfmm_ctx *ctx)
+{
+    return ctx->root_h + std::fabs(ctx->root_c[0]) + std::fabs(ctx->root_c[1]) + std::fabs(ctx->root_c[2]);
+}
+
 // tree: levels partition each layer's points, children partition their parent,
 // centres follow the cell indices, radii bound the points, leaves contain theirs
 void check_tree(const lmfmm_ctx *ctx, Check &ck)
@@ -45,7 +52,7 @@ void check_tree(const lmfmm_ctx *ctx, Check &ck)
     const int L = ctx->med.L, D = ctx->depth;
     const int64_t N = ctx->N, nb = (int64_t)ctx->boxes.size();
     const double h = ctx->root_h;
-    const double sc = h + std::fabs(ctx->root_c[0]) + std::fabs(ctx->root_c[1]) + std::fabs(ctx->root_c[2]);
+    const double sc = coord_scale(ctx);
     int64_t p = 0;
     for (int l = 0; l <= L; ++l) {
         int64_t q = p;
@@ -149,6 +156,7 @@ void check_geometries(const lmfmm_ctx *ctx, Check &ck)
     const int64_t nb = (int64_t)ctx->boxes.size(), npair = (int64_t)ctx->m2l.size();
     const double h = ctx->root_h, theta = ctx->prm.theta, eta = ctx->prm.eta;
     const int nrc = ctx->n_react_comps, ncomp = (int)ctx->comps.size();
+    const double sc = coord_scale(ctx);
     int64_t expect = 0;
     for (size_t gi = 0; gi < ctx->geoms.size(); ++gi) {
         const Geom &G = ctx->geoms[gi];
@@ -166,7 +174,7 @@ void check_geometries(const lmfmm_ctx *ctx, Check &ck)
             continue;
         }
         const CompDev &c = ctx->comps[G.comp];
-        const double Sl = 2.0 * h / (double)(1u << G.level);
+        const double Sl = 2.0 * h / (double)(1u << G.level) + sc;   // tolerance scale
         for (int64_t q = G.pair0; q < G.pair1; ++q) {
             const M2LPair &mp = ctx->m2l[q];
             if (mp.src < 0 || mp.src >= nb || mp.tgt < 0 || mp.tgt >= nb) {
@@ -350,7 +358,7 @@ void check_translations(const lmfmm_ctx *ctx, Check &ck)
             break;
         }
         expect = g.pair1;
-        const double Sc = 2.0 * h / (double)(1u << g.level);
+        const double Sc = 2.0 * h / (double)(1u << g.level) + coord_scale(ctx);   // tolerance scale
         for (int64_t q = g.pair0; q < g.pair1; ++q) {
             const int64_t cb = ctx->tpair_child[q], pb = q < (int64_t)ctx->tpair_parent.size() ? ctx->tpair_parent[q] : -1;
             if (cb < 0 || cb >= nb || pb < 0 || pb >= nb) {

@@ -136,3 +136,22 @@ def test_depth_tuner_picks_the_benchmark_depth():
     best, pred = lmfmm.plan_depth(w.d, w.k, w.xyz, p=12, depths=(5, 6, 7), theta=0.5)
     assert best == 6 and min(pred, key=pred.get) == 6
     assert 9.0 < pred[6] < 14.0    # measured: 11.3 ms per matvec at depth 6
+
+
+def test_degenerate_inputs():
+    """One point; one layer (no interface: no reaction component, the free-space
+    part only); the root as the only leaf; two points a thousand units apart
+    (a root cell far larger than either leaf)."""
+    rc, info = lmfmm.plan_check([0.0], [1, 2], [[0.1, 0.2, 0.3]], p=4, depth=2, components=lmfmm.TOTAL)
+    assert rc == lmfmm.OK, info["message"]
+    assert info["n_leaves"] == [1, 0] and info["n_leaf_pairs_checked"] == 1 + 1   # one reaction, one free
+    rng = np.random.default_rng(0)
+    x = rng.uniform(-1, 1, (300, 3))
+    rc, info = lmfmm.plan_check([], [1.0 + 0j], x, p=4, depth=3, components=lmfmm.TOTAL)
+    assert rc == lmfmm.OK and info["n_components"] == 0 and info["n_free_components"] == 1
+    assert info["n_leaf_pairs_checked"] == info["n_leaves"][0] ** 2
+    rc, info = lmfmm.plan_check([0.0], [1, 2], x, p=4, depth=0, components=lmfmm.TOTAL)
+    assert rc == lmfmm.OK and info["n_far_pairs"] == 0 and info["n_free_far_pairs"] == 0
+    rc, info = lmfmm.plan_check([0.0], [1, 2], [[0.1, 0.2, 0.3], [1e3, 0, -5]], p=4, depth=4,
+                                components=lmfmm.TOTAL)
+    assert rc == lmfmm.OK, info["message"]
