@@ -345,6 +345,8 @@ typedef struct {
     int64_t n_leaf_pairs_checked;   /* (component, source leaf, target leaf) triples covered */
     int64_t n_violations;           /* failed checks (0: consistent) */
     double root_center[3], root_half;  /* root cell; leaves have side 2 root_half / 2^depth */
+    int64_t n_geometries_level[21]; /* reaction M2L tables per tree level, all components */
+    int64_t max_geometries_component_level;  /* most tables of one (component, level) */
     char message[256];              /* first failure or argument error, else empty */
 } lmfmm_plan_info;
 

@@ -474,11 +474,18 @@ extern "C" lmfmm_status lmfmm_plan_check(const lmfmm_params *prm, int L, const d
     out->n_free_components = (int)ctx->comps.size() - ctx->n_react_comps;
     out->n_boxes = (int64_t)ctx->boxes.size();
     for (int l = 0; l <= ctx->med.L && l < 9; ++l) out->n_leaves[l] = ctx->lvl1[l][D] - ctx->lvl0[l][D];
+    std::vector<int64_t> per_cl((size_t)ctx->n_react_comps * (D + 1), 0);
     for (size_t gi = 0; gi < ctx->geoms.size(); ++gi) {
         const int64_t n = ctx->geoms[gi].pair1 - ctx->geoms[gi].pair0;
         if (gi < ctx->n_react_geoms) {
             out->n_geometries++;
             out->n_far_pairs += n;
+            const int lev = ctx->geoms[gi].level, c = ctx->geoms[gi].comp;
+            if (lev >= 0 && lev <= D && lev < 21 && c >= 0 && c < ctx->n_react_comps) {
+                out->n_geometries_level[lev]++;
+                const int64_t v = ++per_cl[(size_t)c * (D + 1) + lev];
+                out->max_geometries_component_level = std::max(out->max_geometries_component_level, v);
+            }
         } else {
             out->n_free_geometries++;
             out->n_free_far_pairs += n;

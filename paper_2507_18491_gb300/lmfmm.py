@@ -61,7 +61,8 @@ class PlanInfo(ctypes.Structure):
                 ("n_translation_pairs", ctypes.c_int64), ("n_work_items", ctypes.c_int64),
                 ("n_columns", ctypes.c_int64), ("n_leaf_pairs_checked", ctypes.c_int64),
                 ("n_violations", ctypes.c_int64), ("root_center", ctypes.c_double * 3),
-                ("root_half", ctypes.c_double), ("message", ctypes.c_char * 256)]
+                ("root_half", ctypes.c_double), ("n_geometries_level", ctypes.c_int64 * 21),
+                ("max_geometries_component_level", ctypes.c_int64), ("message", ctypes.c_char * 256)]
 
 
 EXPORTS = ["lmfmm_default_params", "lmfmm_create", "lmfmm_set_layers", "lmfmm_set_points",
@@ -341,8 +342,9 @@ def plan_check(d, k, xyz, p=8, depth=-1, leaf_cap=64, theta=0.55, eta=0.1, compo
                                  karr, int(xyz.shape[0]), xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                  int(flags), ctypes.byref(info))
     out = {f: getattr(info, f) for f, _ in PlanInfo._fields_
-           if f not in ("n_leaves", "root_center", "message")}
+           if f not in ("n_leaves", "root_center", "message", "n_geometries_level")}
     out["n_leaves"] = list(info.n_leaves)[:d.size + 1]
+    out["n_geometries_level"] = list(info.n_geometries_level)[:info.depth + 1]
     out["root_center"] = list(info.root_center)
     out["message"] = info.message.decode()
     return rc, out

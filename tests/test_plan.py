@@ -58,6 +58,8 @@ def test_every_leaf_pair_is_split_exactly_once(name):
     assert info["n_columns"] == 9 * info["n_far_pairs"]
     assert info["n_work_items"] >= -(-info["n_columns"] // 64)
     assert info["n_near_pairs"] > 0 and info["n_far_pairs"] > 0
+    assert sum(info["n_geometries_level"]) == info["n_geometries"]
+    assert 0 < info["max_geometries_component_level"] <= info["n_geometries"]
 
 
 @pytest.mark.parametrize("name", ["two_layer_n512", "paper_3layer_m20000", "batch_problem_auto_depth"])
