@@ -296,6 +296,10 @@ lmfmm_status lmfmm_translation_matrix(int p, lmfmm_c128 k, const double *t, lmfm
 lmfmm_status lmfmm_free_m2l_table(int p, lmfmm_c128 k, double rho, double dz, lmfmm_c128 *tables,
                                    lmfmm_c128 *blocks);
 
+/* Counts of the built context and the timings of its last build and matvec
+ * (fields above; the stage times are CUDA-event intervals on the matvec's
+ * stream, filled in once its last event has completed, else those of the
+ * previous matvec).  No synchronisation.  *out is caller-owned. */
 lmfmm_status lmfmm_get_stats(const lmfmm_ctx *ctx, lmfmm_stats *out);
 
 /* ------------------------------------------------------------- plan check
