@@ -296,6 +296,30 @@ lmfmm_status lmfmm_translation_matrix(int p, lmfmm_c128 k, const double *t, lmfm
 lmfmm_status lmfmm_free_m2l_table(int p, lmfmm_c128 k, double rho, double dz, lmfmm_c128 *tables,
                                    lmfmm_c128 *blocks);
 
+/* Host-only (no device, no context): the Chebyshev form of the normalised
+ * associated Legendre functions that the M2L tabulation uses (Appendix B).
+ * For 0 <= m <= n <= p (1 <= p <= 16), with t = n (n + 1) / 2 + m and
+ * K = (p + 1) / 2, B[t][0 .. K] (caller-owned, (p+1)(p+2)/2 x (K+1) doubles)
+ * holds the coefficients with
+ *     P^_n^m(cos b) = tau_nm(b) sum_j B[t][j] T_j(cos 2b),
+ *     tau_nm = 1 (n, m even), 1 / cos b (n odd, m even), sin b (n, m odd),
+ *              sin b / cos b (n even, m odd),
+ * an identity of polynomials in (cos b, sin b), so it holds for the complex
+ * angles of the Sommerfeld integrals (cos b = k_z / k, sin b = k_rho / k);
+ * entries past a function's degree are 0. */
+lmfmm_status lmfmm_legendre_chebyshev(int p, double *B);
+
+/* Host-only: the product tensor of eqs. legendre_Q_v / legendre_Q_w that the
+ * tabulation contracts with the Chebyshev integrals (Section 3.4 with Appendix
+ * A's C^{ab} re-expansion of T_j(a x + b)): for source and target wavenumbers
+ * k, kp and every source index s = (n', m') and target index t = (nu, mu)
+ * (triangle indices as above, T = (p+1)(p+2)/2), G[s][t][0 .. p+1]
+ * (caller-owned, T x T x (p+2) complex) satisfies
+ *     f_s(b) f_t(b') = sum_l G[s][t][l] T_l(cos 2 b0),
+ * f = P^ / tau of lmfmm_legendre_chebyshev, cos 2b = 1 - 2 k_rho^2 / k^2,
+ * cos 2b' = 1 - 2 k_rho^2 / kp^2, b0 the angle of the smaller of |k|, |kp|. */
+lmfmm_status lmfmm_legendre_product(int p, lmfmm_c128 k, lmfmm_c128 kp, lmfmm_c128 *G);
+
 /* Counts of the built context and the timings of its last build and matvec
  * (fields above; the stage times are CUDA-event intervals on the matvec's
  * stream, filled in once its last event has completed, else those of the

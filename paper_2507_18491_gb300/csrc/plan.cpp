@@ -558,3 +558,28 @@ extern "C" lmfmm_status lmfmm_plan_depth(const lmfmm_params *prm, int L, const d
     }
     return LMFMM_OK;
 }
+
+// The Chebyshev machinery of Appendices A and B exactly as the M2L tabulation
+// builds it (host routines bcoef_table and gtensor), for unit tests of those
+// routines against independent Legendre functions.
+extern "C" lmfmm_status lmfmm_legendre_chebyshev(int p, double *B)
+{
+    if (p < 1 || p > 16 || !B) return LMFMM_ERR_ARG;
+    std::vector<double> b;
+    bcoef_table(p, (p + 1) / 2, b);
+    std::copy(b.begin(), b.end(), B);
+    return LMFMM_OK;
+}
+
+extern "C" lmfmm_status lmfmm_legendre_product(int p, lmfmm_c128 k, lmfmm_c128 kp, lmfmm_c128 *G)
+{
+    if (p < 1 || p > 16 || !G || (k.re == 0 && k.im == 0) || (kp.re == 0 && kp.im == 0) ||
+        !std::isfinite(k.re) || !std::isfinite(k.im) || !std::isfinite(kp.re) || !std::isfinite(kp.im))
+        return LMFMM_ERR_ARG;
+    std::vector<double> b;
+    const int KM = (p + 1) / 2;
+    bcoef_table(p, KM, b);
+    static_assert(sizeof(cd) == sizeof(lmfmm_c128), "complex layouts agree");
+    gtensor(p, b, KM, zc(k.re, k.im), zc(kp.re, kp.im), reinterpret_cast<cd *>(G));
+    return LMFMM_OK;
+}

@@ -69,7 +69,7 @@ EXPORTS = ["lmfmm_default_params", "lmfmm_create", "lmfmm_set_layers", "lmfmm_se
            "lmfmm_set_points_device", "lmfmm_build", "lmfmm_matvec", "lmfmm_matvec_host",
            "lmfmm_matvec_adjoint", "lmfmm_matvec_transpose", "lmfmm_gradient", "lmfmm_check", "lmfmm_test_set_status", "lmfmm_direct",
            "lmfmm_direct_noalloc", "lmfmm_densities", "lmfmm_m2l_table", "lmfmm_translation_matrix",
-           "lmfmm_free_m2l_table",
+           "lmfmm_free_m2l_table", "lmfmm_legendre_chebyshev", "lmfmm_legendre_product",
            "lmfmm_get_stats", "lmfmm_plan_check", "lmfmm_plan_depth", "lmfmm_last_error", "lmfmm_destroy", "lmfmm_batch_create",
            "lmfmm_batch_matvec", "lmfmm_batch_tune", "lmfmm_batch_check", "lmfmm_batch_info",
            "lmfmm_batch_last_error", "lmfmm_batch_destroy"]
@@ -117,6 +117,8 @@ def load():
         "lmfmm_translation_matrix": [i, _Complex128, ctypes.POINTER(d), P, P],
         "lmfmm_free_m2l_table": [i, _Complex128, d, d, P, P],
         "lmfmm_get_stats": [P, ctypes.POINTER(Stats)],
+        "lmfmm_legendre_chebyshev": [i, P],
+        "lmfmm_legendre_product": [i, _Complex128, _Complex128, P],
         "lmfmm_plan_check": [ctypes.POINTER(Params), i, ctypes.POINTER(d), ctypes.POINTER(_Complex128), i64,
                              ctypes.POINTER(d), i, ctypes.POINTER(PlanInfo)],
         "lmfmm_plan_depth": [ctypes.POINTER(Params), i, ctypes.POINTER(d), ctypes.POINTER(_Complex128), i64,
@@ -316,6 +318,23 @@ def free_m2l_table(p, k, rho, dz, blocks=False):
                                        float(rho), float(dz), ctypes.c_void_p(tab.ctypes.data),
                                        ctypes.c_void_p(blk.ctypes.data) if blocks else None))
     return tab, blk
+
+
+def legendre_chebyshev(p):
+    """B[(p+1)(p+2)/2][(p+1)//2 + 1] of lmfmm_legendre_chebyshev (host only)."""
+    B = np.zeros(((p + 1) * (p + 2) // 2, (p + 1) // 2 + 1))
+    _check(load().lmfmm_legendre_chebyshev(int(p), ctypes.c_void_p(B.ctypes.data)))
+    return B
+
+
+def legendre_product(p, k, kp):
+    """G[T][T][p+2] of lmfmm_legendre_product (host only)."""
+    T = (p + 1) * (p + 2) // 2
+    G = np.zeros((T, T, p + 2), np.complex128)
+    _check(load().lmfmm_legendre_product(int(p), _Complex128(float(np.real(k)), float(np.imag(k))),
+                                         _Complex128(float(np.real(kp)), float(np.imag(kp))),
+                                         ctypes.c_void_p(G.ctypes.data)))
+    return G
 
 
 def get_stats(ctx) -> dict:
