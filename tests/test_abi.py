@@ -69,3 +69,15 @@ def test_null_context_is_an_argument_error(lib):
     assert lib.lmfmm_test_set_status(None, 4) == lmfmm.ERR_ARG
     assert lib.lmfmm_matvec(None, None, lmfmm.C128, None, None) == lmfmm.ERR_ARG
     assert lib.lmfmm_set_points_device(None, 1, None, None) == lmfmm.ERR_ARG
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    """No fallback: without the compiled library every entry point raises."""
+    monkeypatch.setattr(lmfmm, "_lib", None)
+    monkeypatch.setattr(lmfmm, "library_path", lambda: str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        lmfmm.load()
+    with pytest.raises(RuntimeError, match="not built"):
+        lmfmm.default_params()
+    with pytest.raises(RuntimeError, match="not built"):
+        lmfmm.plan_check([0.0], [1, 2], [[0.1, 0.2, 0.3]])
